@@ -9,7 +9,11 @@ states only that a conjugate gradient method solves it; the details below are a 
   the system is consistent (b is orthogonal to the constants);
 * preconditioner W^{-1} (the inverse of the diagonal X-space mass matrix, Eq. diagonal);
 * stopping rule  r . W^{-1} r <= tol^2 * b . W^{-1} b  (relative residual in the
-  discrete L2 norm of Eq. def_norm), or a fixed iteration count (parity mode).
+  discrete L2 norm of Eq. def_norm), or a fixed iteration count (parity mode).  The rule is
+  on the true residual b - A x: when the recursively updated residual of CG meets it, the
+  true residual is computed; if that one does not, CG restarts from it (p = W^{-1} r), at
+  most MAX_RESTARTS times.  (Over thousands of iterations the recursive residual drifts away
+  from the true one by rounding.)
 
 With x0 of W-mean zero all iterates stay W-mean zero, since every update direction
 z = W^{-1} r satisfies sum W z = sum r = 0.
@@ -22,6 +26,9 @@ def poisson_rhs(ops, omega):
     W = ops.W2
     mean = float(np.sum(W * omega)) / float(np.sum(W))
     return W * (omega - mean)
+
+
+MAX_RESTARTS = 20
 
 
 class CGResult:
@@ -45,13 +52,25 @@ def pcg(ops, b, x0, tol, maxit, fixed_iters=0):
     p = z.copy()
     rho = float(np.sum(r * z))
     it = 0
+    restarts = 0
     converged = True
     while True:
         if fixed_iters > 0:
             if it == fixed_iters:
                 break
         elif rho <= tol * tol * rho_b:
-            break
+            r_true = b - ops.A(x)
+            rho_true = float(np.sum(r_true * r_true / W))
+            if rho_true <= tol * tol * rho_b or restarts == MAX_RESTARTS:
+                rho = rho_true
+                converged = rho_true <= tol * tol * rho_b
+                break
+            restarts += 1
+            r = r_true
+            z = r / W
+            p = z.copy()
+            rho = float(np.sum(r * z))
+            continue
         if rho == 0.0:
             break
         if it == maxit:
