@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Throughput of the conservative dG-Arakawa Navier-Stokes time step on GB300 GPUs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision fp64|mixed] [--impl native|reference] [--no-cpu-baseline]
+
+A step is one time step of the whole hot path: the Arakawa bracket + viscous term + AB3
+update (one fused kernel) and the CG Poisson solve (one persistent cooperative kernel), on
+synthetic fields shaped like the paper's runs.  Default workload (the large single run):
+512 x 512 periodic cells on [0, 2pi]^2, n = 4 nodes per dimension (4.19M dof), double shear
+layer, D = 1e-4, dt = 5e-4, CG tolerance 1e-10, float64.
+
+Prints ONE JSON line on rank 0.  value = dof * steps / device seconds, summed over ranks
+(each rank advances its own replica: the simulations are independent units, no collective is
+in the data path).  --impl reference times the FP64 NumPy oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: cells per side, n, viscosity, dt, CG tol, initial field
+    "shear512_n4": dict(N=512, n=4, D=1e-4, dt=5e-4, tol=1e-10, field="shear_layer"),
+    "sinsin32_n3": dict(N=32, n=3, D=0.0, dt=1e-3, tol=1e-12, field="sin_sin_noise"),
+    "random1024_n5": dict(N=1024, n=5, D=0.0, dt=2e-4, tol=1e-10, field="random_phase"),
+}
+DEFAULT_WORKLOAD = "shear512_n4"
+L2_BYTES = 129 * 1024 * 1024
+# FP64 FMA peak of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (recipe's unit counts
+# and maximum SM clock; the microbenchmark of the design doc measured 1.20 TFLOP/s at ~2.0 GHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_field(name, X, Y):
+    from paper_1311_7477_gb300 import fields
+    if name == "shear_layer":
+        return fields.shear_layer(X, Y)
+    if name == "sin_sin_noise":
+        return fields.sin_sin_noise(X, Y, amp=1e-3, seed=0)
+    if name == "random_phase":
+        return fields.random_phase(X, Y, seed=1)
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = str(gpu_index)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[3], parts[4], parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[4]) if v.lower() == "active"})
+        try:
+            pw = max(float(r[2]) for r in rows)
+        except ValueError:
+            pw = None
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "reasons": reasons, "samples": len(rows),
+                "power_w_max": pw}
+
+
+def _gpu_index_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+# ----------------------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------------
+SAMPLE_CELLS = 128
+
+
+def oracle_sample(wl, cg_sample_iters=4):
+    """Times the FP64 oracle on a SAMPLE_CELLS^2 periodic grid of the same n, field and
+    parameters: one right-hand side (bracket + viscous term + AB3 update), the Poisson setup
+    and cg_sample_iters CG iterations.  Returns seconds per dof for each part (the oracle's
+    cost is linear in the dof count)."""
+    import numpy as np
+    from oracle.operators import Operators
+    from oracle.solver import pcg, poisson_rhs
+    from oracle.tables import Grid
+    g = Grid(SAMPLE_CELLS, SAMPLE_CELLS, wl["n"])
+    ops = Operators(g)
+    X, Y = g.mesh()
+    w = make_field(wl["field"], X, Y)
+    psi = 0.01 * np.sin(X) * np.cos(Y)
+    R1 = np.zeros_like(w)
+    dof = w.size
+    t0 = time.perf_counter()
+    R = -ops.bracket(psi, w)
+    if wl["D"] != 0.0:
+        R = R + wl["D"] * ops.laplacian(w)
+    w1 = w + wl["dt"] * (23.0 * R - 16.0 * R1 + 5.0 * R1) / 12.0
+    t1 = time.perf_counter()
+    b = poisson_rhs(ops, w1)
+    t2 = time.perf_counter()
+    pcg(ops, b, psi, 1e-30, cg_sample_iters, fixed_iters=cg_sample_iters)
+    t3 = time.perf_counter()
+    # pcg includes one setup apply (r0 = b - A x0) besides the iterations
+    return {"rhs_s_per_dof": (t1 - t0) / dof, "setup_s_per_dof": (t2 - t1) / dof,
+            "cg_s_per_dof_iter": (t3 - t2) / dof / (cg_sample_iters + 1), "sample_dof": dof}
+
+
+def oracle_iters_per_step(name):
+    path = os.path.join(ROOT, "tests", "golden", "cg_iterations_shear512_n4.json")
+    if name == "shear512_n4" and os.path.exists(path):
+        d = json.load(open(path))
+        if d.get("ab3_iters_mean"):
+            return float(d["ab3_iters_mean"]), "the oracle's own CG iterations per AB3 step on this workload"
+    return None, None
+
+
+def cpu_baseline(name, wl, native_iters):
+    """Runs the oracle sample single-threaded in a child process; returns the cpu_baseline
+    object of the JSON line."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0,%r); import bench; "
+            "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r])))" % (ROOT, name))
+    t0 = time.time()
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + out.stderr.strip()[-200:]}
+    s = json.loads(out.stdout.strip().splitlines()[-1])
+    k, ksrc = oracle_iters_per_step(name)
+    if k is None:
+        k, ksrc = native_iters, "CG iterations per step measured on the GPU in this run"
+    sec_per_dof_step = s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"]
+    return {"value": 1e-6 / sec_per_dof_step, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
+            "sample": ("FP64 NumPy oracle, single thread, on a %dx%d-cell grid (n=%d, %d dof): one RHS "
+                       "(bracket + viscous term + AB3 update), the Poisson setup and 5 CG operator "
+                       "applications, timed per dof and scaled to one step of %.0f CG iterations (%s); "
+                       "%.1f s of CPU" % (SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], k, ksrc,
+                                           time.time() - t0)),
+            "parts_s_per_dof": s}
+
+
+def run_reference(args, wl, name):
+    """--impl reference: the oracle on the host cores, each step one bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    k, ksrc = oracle_iters_per_step(name)
+    if k is None:
+        k, ksrc = 200.0, "assumed 200 CG iterations per step (no measured count for this workload)"
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1)
+    t0 = time.perf_counter()
+    secs = []
+    for _ in range(args.steps):
+        s = oracle_sample(wl, 1)
+        secs.append(s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"])
+    wall = time.perf_counter() - t0
+    dof = wl["N"] * wl["N"] * wl["n"] ** 2
+    sec_per_step = sum(secs) / len(secs) * dof
+    value = dof / sec_per_step / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or 1
+    line = {"impl": "reference", "metric": "Mdof·steps/s", "value": value, "unit": "Mdof·steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(name, wl, "fp64"),
+            "cpu_baseline": {"value": value, "unit": "Mdof·steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: oracle RHS + Poisson setup + 2 CG applications on a %dx%d-cell "
+                                       "grid, scaled per dof to %dx%d cells and %.0f CG iterations (%s); %.1f s wall"
+                                       % (SAMPLE_CELLS, SAMPLE_CELLS, wl["N"], wl["N"], k, ksrc, wall)},
+            "e2e": {"value": value, "unit": "Mdof·steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _config(name, wl, precision):
+    dof = wl["N"] * wl["N"] * wl["n"] ** 2
+    return {"workload": name, "cells": "%dx%d" % (wl["N"], wl["N"]), "n": wl["n"], "dof": dof,
+            "domain": "[0,2pi]^2 periodic", "field": wl["field"], "D": wl["D"], "dt": wl["dt"],
+            "cg_tol": wl["tol"], "precision": precision, "parallelism": "replicas (one simulation per GPU)"}
+
+
+# ----------------------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, args.workload)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3 (the first two steps are RK4 start-up steps)")
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_1311_7477_gb300 import build as _build
+    _build.build()
+    from paper_1311_7477_gb300 import dg, fields
+
+    precision = dg.DG_FP64 if args.precision == "fp64" else dg.DG_MIXED
+    N, n = wl["N"], wl["n"]
+    g = dg.Grid(N, N, n)
+    dof = g.dof
+    xn, yn, _ = g.nodes()
+    X, Y = fields.mesh_from_nodes(xn, yn)
+    w0 = make_field(wl["field"], X, Y)
+    stream = torch.cuda.current_stream()
+    w0_dev = torch.from_numpy(w0).cuda()
+    sim = dg.Sim(g, w0_dev, D=wl["D"], dt=wl["dt"], precision=precision, cg_tol=wl["tol"], cg_maxit=200000)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (includes the two RK4 start-up steps)
+    sim.step(args.warmup)
+    info0 = sim.status()
+    sim.set_timing(True)
+    sampler = ClockSampler(_gpu_index_for_smi(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    info1 = sim.status()
+    cnt = sim.counters()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = (info1.cg_iters_total - info0.cg_iters_total) / max(args.steps, 1)
+
+    # --- end to end through the host-buffer entry points: resume a checkpoint from pinned
+    # host memory, step with the invariants read back every step, download omega and psi.
+    ke = args.e2e_steps or max(3, min(args.steps, 10))
+    shape = g.shape
+    dstate = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+    step_k = sim.get_state(*dstate)
+    hstate = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(5)]
+    for h, d in zip(hstate, dstate):
+        h.copy_(d)
+    hout = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    barrier()
+    t0 = time.perf_counter()
+    sim.upload(step_k, *hstate)
+    for _ in range(ke):
+        sim.step(1)
+        sim.invariants()
+    sim.download(hout[0], hout[1])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # --- mixed precision: error of one step against the float64 path from the identical state
+    err_vs_fp64 = None
+    if precision == dg.DG_MIXED:
+        st = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+        kk = sim.get_state(*st)
+        ref = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=dg.DG_FP64, cg_tol=wl["tol"], cg_maxit=200000)
+        ref.set_state(kk, *st)
+        sim.set_state(kk, *st)
+        ref.step(1)
+        sim.step(1)
+        wa, pa = torch.empty_like(st[0]), torch.empty_like(st[0])
+        wb, pb = torch.empty_like(st[0]), torch.empty_like(st[0])
+        ref.get(wa, pa)
+        sim.get(wb, pb)
+        torch.cuda.synchronize()
+        err_vs_fp64 = {"omega_rel_l2": float(torch.linalg.norm(wa - wb) / torch.linalg.norm(wa)),
+                       "psi_rel_l2": float(torch.linalg.norm(pa - pb) / torch.linalg.norm(pa)),
+                       "what": "one step from the identical state, mixed vs the float64 path (which matches "
+                               "the FP64 oracle to 1e-12 per step)",
+                       "refine_sweeps_last": int(sim.status().refine_sweeps_last)}
+        ref.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    value = dof * args.steps * world / (ms / 1e3) / 1e6
+    peaks, peak_src = measured_peaks()
+    # roofline of the dominant kernel (the persistent CG solve), from its live event timing
+    cg_ms_per_launch = cnt.cg_ms / max(cnt.cg_launches, 1)
+    rhs_ms_per_launch = cnt.rhs_ms / max(cnt.rhs_launches, 1)
+    it_per_launch = (info1.cg_iters_total - info0.cg_iters_total) / max(cnt.cg_launches, 1)
+    flops_iter = 4 * (n + 4) + 10      # Ahat apply (rank-one faces) + 5 vector updates/dots, per dof
+    flops_setup = 4 * (n + 4) + 8
+    bytes_iter = 8 * 8                 # x, r, p read+write; q write+read (float64)
+    bytes_setup = 6 * 8
+    cg_flops = dof * (flops_iter * it_per_launch + flops_setup)
+    cg_bytes = dof * (bytes_iter * it_per_launch + bytes_setup)
+    achieved_tf = cg_flops / (cg_ms_per_launch / 1e3) / 1e12
+    achieved_gbs = cg_bytes / (cg_ms_per_launch / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "cg_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(args.workload, {}).get(args.precision)
+        except (OSError, ValueError):
+            traffic = None
+    roof = {"kernel": "cg_kernel (persistent CG Poisson solve)", "bound": "alu",
+            "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz",
+            "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
+            "launch_ms": cg_ms_per_launch, "iters_per_launch": it_per_launch,
+            "algorithmic_per_dof": {"flops_per_iter": flops_iter, "bytes_per_iter": bytes_iter}}
+    line = {"metric": "Mdof·steps/s", "value": value, "unit": "Mdof·steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": dict(_config(args.workload, wl, args.precision),
+                           l2=("no flush: the per-step working set (%.0f MB of state and CG vectors) exceeds "
+                               "the 129 MB L2" % (12 * dof * 8 / 1e6))),
+            "cg_iters_per_step": iters, "rhs_ms": rhs_ms_per_launch, "roofline": roof,
+            "error_vs_fp64": err_vs_fp64,
+            "gpu_launches": int(cnt.launches), "clocks": clocks,
+            "e2e": {"value": dof * ke * world / e2e_s / 1e6, "unit": "Mdof·steps/s",
+                    "h2d_bytes_per_step": int(5 * dof * 8 / ke), "d2h_bytes_per_step": int(2 * dof * 8 / ke) + 24,
+                    "steps": ke,
+                    "what": "upload of the full stepper state from pinned host memory, %d steps each followed "
+                            "by a host read of (V, E, Omega), download of omega and psi" % ke}}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, wl, iters)
+    else:
+        line["cpu_baseline"] = None
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

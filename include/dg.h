@@ -1,0 +1,228 @@
+/*
+ * dg.h -- C ABI of libdgk: the conservative dG-Arakawa discretisation of the 2D
+ * incompressible Navier-Stokes equations in vorticity / stream-function form
+ *
+ *     d omega/dt + {psi, omega} = D Delta omega,     -Delta psi = omega     (Eq. vorticity)
+ *
+ * on a periodic Cartesian grid of Nx x Ny square-or-rectangular cells with n Gauss-Legendre
+ * nodes per cell and dimension (polynomial degree n-1, 1 <= n <= 5; Sec. 4.1), as CUDA
+ * kernels for one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions
+ * -----------
+ * - Every function returns an int status (DG_OK = 0 or one of DG_ERR_*); none aborts or
+ *   prints.  dg_last_error() returns a message for the last failure on the calling thread.
+ * - Fields are arrays of Nx*Ny*n*n values of X-space data (the field at the Gauss nodes of
+ *   every cell, Sec. 4.1/4.2) in the cell-blocked layout
+ *       idx = ((cy * Nx + cx) * n + a) * n + b
+ *   cy, cx = cell row / column, a = y-node, b = x-node; node (a, b) of cell (cy, cx) sits at
+ *       x = (cx + 1/2) hx + hx/2 * x_b,  y = (cy + 1/2) hy + hy/2 * x_a,  hx = Lx/Nx, hy = Ly/Ny.
+ * - Field pointers passed to the compute calls are DEVICE pointers owned by the caller,
+ *   8-byte aligned, non-overlapping unless stated.  The library owns only the memory behind
+ *   its handles (dg_grid, dg_sim, dg_batch).
+ * - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *   asynchronous on that stream except those that return host scalars, which synchronise it.
+ * - Calls on one handle must not run concurrently with each other (handles own workspace).
+ */
+#ifndef DGK_DG_H
+#define DGK_DG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define DG_OK 0
+#define DG_ERR_ARG 1        /* invalid argument: size, pointer, alignment, parameter range  */
+#define DG_ERR_CUDA 2       /* a CUDA runtime call failed (no device, launch failure, ...) */
+#define DG_ERR_NOMEM 3      /* device or host allocation failed / over budget              */
+#define DG_ERR_NOCONV 4     /* CG reached maxit before the tolerance                       */
+#define DG_ERR_NONFINITE 5  /* a reduction saw a NaN or Inf                                */
+#define DG_ERR_TIMEOUT 6    /* a device-side wait hit its iteration cap                    */
+
+/* ---- precision modes ------------------------------------------------------------- */
+#define DG_FP64 0   /* everything in float64                                               */
+#define DG_MIXED 1  /* bracket and inner CG in float32, float64 refinement, state and sums */
+
+typedef struct dg_grid dg_grid;
+typedef struct dg_sim dg_sim;
+typedef struct dg_batch dg_batch;
+
+/* Message for the last error on this thread ("" if none).  Never NULL. */
+const char* dg_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int dg_version(void);
+
+/*
+ * dg_ref_tables -- host-only: the dimensionless per-n tables the kernels are built from
+ * (Sec. 4.1: Gauss-Legendre x_j, w_j by Newton's method on the Legendre recursion,
+ * Eq. recursion; Sec. 4.2: the central-flux derivative blocks; Sec. 6: the LDG blocks).
+ * out receives, in this order (doubles):
+ *   x[n], w[n], C0[n*n], muR[n], muL[n], lL[n], lR[n], A1cc[n*n], betaA[n]
+ * with  h (f_x)_c = C0 f_c + muR (lL . f_{c+1}) - muL (lR . f_{c-1})        (central flux)
+ *       h (A1 u)_c = A1cc u_c + betaA (lL . u_{c+1}) + lL (betaA . u_{c-1}) (LDG, 1D)
+ * out_len must be at least dg_ref_tables_len(n) = 7n + 2n^2.
+ * Errors: DG_ERR_ARG for n outside 1..5, tau < 0, out NULL or out_len too small.
+ */
+int dg_ref_tables_len(int n);
+int dg_ref_tables(int n, double tau, double* out, int out_len);
+
+/*
+ * dg_grid_create -- periodic grid [0,Lx] x [0,Ly] with Nx x Ny cells and n nodes per cell
+ * and dimension (Sec. 4.1), LDG jump penalty tau >= 0 (Sec. 6; tau = 0 is the plain
+ * alternating-flux LDG).  Allocates the grid's device workspace on the current device.
+ * Errors: DG_ERR_ARG (n outside 1..5, Nx or Ny < 1, Lx or Ly <= 0, tau < 0, g NULL),
+ * DG_ERR_NOMEM, DG_ERR_CUDA.
+ */
+int dg_grid_create(dg_grid** g, int Nx, int Ny, int n, double Lx, double Ly, double tau);
+int dg_grid_destroy(dg_grid* g);
+
+/* Number of values of one field: Nx*Ny*n*n (0 if g is NULL). */
+long long dg_grid_dof(const dg_grid* g);
+
+/*
+ * dg_grid_nodes -- host arrays: x node coordinates (Nx*n, index cx*n+b), y node coordinates
+ * (Ny*n, index cy*n+a) and the 2D quadrature weights of one cell, W_ab = (hy w_a/2)(hx w_b/2)
+ * (n*n, Eq. def_norm).  Any pointer may be NULL.
+ */
+int dg_grid_nodes(const dg_grid* g, double* x_nodes, double* y_nodes, double* weights);
+
+/*
+ * dg_grid_set_tiles -- override the kernels' cell tile (TY x TX cells per thread block);
+ * 0 restores the built-in choice for this n.  Used by the autotuner.  Errors: DG_ERR_ARG.
+ */
+int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
+
+/*
+ * dg_bracket -- J = {psi, omega} by the conservative dG Arakawa bracket
+ *     J = (J++ + J+x + Jx+) / 3                                   (Eq. J, Sec. 3)
+ * with the central-flux dG derivatives of Eq. discrete_der / Eq. matrix_xspace and
+ * pointwise X-space products (Sec. 4.2).  float64.  J must not alias psi or omega.
+ */
+int dg_bracket(dg_grid* g, const double* psi, const double* omega, double* J, void* stream);
+
+/*
+ * dg_laplace_apply -- the matrix-free LDG operator of Sec. 6 (alternating fluxes, penalty
+ * tau): mode 0 writes y = A x with A = W (x) A1 + A1 (x) W symmetric positive semi-definite
+ * (kernel = constants); mode 1 writes y = Delta_h x = -W^{-1} A x.  float64.  y must not
+ * alias x.  Errors: DG_ERR_ARG for another mode.
+ */
+int dg_laplace_apply(dg_grid* g, const double* x, double* y, int mode, void* stream);
+
+/*
+ * dg_poisson_solve -- -Delta_h psi = omega - mean_W(omega) by conjugate gradients (Sec. 6)
+ * on A psi = W (omega - mean), preconditioned by W^{-1} (run as plain CG on the symmetric
+ * scaling W^{-1/2} A W^{-1/2}), from the initial guess in psi.  Stops when
+ * r.W^{-1}r <= tol^2 b.W^{-1}b, or after exactly fixed_iters iterations if fixed_iters > 0
+ * (parity mode; tol is then ignored).  The whole loop runs in one persistent cooperative
+ * kernel; every device-side wait is capped.  float64.  Synchronises the stream.
+ * iters / relres (may be NULL) receive the iteration count and sqrt(r.W^{-1}r / b.W^{-1}b).
+ * Errors: DG_ERR_ARG (tol <= 0 with fixed_iters == 0, maxit < 0), DG_ERR_NOCONV (psi then
+ * holds the last iterate), DG_ERR_TIMEOUT, DG_ERR_CUDA.
+ */
+int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, int maxit,
+                     int fixed_iters, int* iters, double* relres, void* stream);
+
+/*
+ * dg_invariants -- out[0..2] = (V, E, Omega) = (int omega, 1/2 int psi omega,
+ * 1/2 int omega^2) by Gauss-Legendre quadrature (Eq. quantities, Eq. def_norm), summed in
+ * float64 in a fixed order.  Synchronises the stream.  Errors: DG_ERR_NONFINITE if a sum is
+ * not finite (out is still written).
+ */
+int dg_invariants(dg_grid* g, const double* psi, const double* omega, double out[3], void* stream);
+
+/* ---- simulations: the time stepper of Sec. 6 ---------------------------------------- */
+
+typedef struct {
+  long long step;            /* completed time steps                                        */
+  long long cg_iters_total;  /* CG iterations over all solves since creation                */
+  int cg_iters_last;         /* iterations of the last Poisson solve                        */
+  int cg_iters_max;          /* largest iteration count of any solve                        */
+  double cg_relres_last;     /* sqrt(r.W^-1 r / b.W^-1 b) at the end of the last solve      */
+  int refine_sweeps_last;    /* float64 refinement sweeps of the last solve (DG_MIXED)      */
+  int status;                /* first error seen by a device-side solve (DG_OK if none)    */
+} dg_sim_info;
+
+/*
+ * dg_sim_create -- a simulation on grid g (which must outlive it) with viscosity D >= 0,
+ * time step dt > 0, precision DG_FP64 or DG_MIXED, CG tolerance cg_tol > 0 and iteration
+ * cap cg_maxit, from the device field omega0.  Solves for psi0 at creation.  The scheme is
+ * the explicit 3-step Adams-Bashforth method (Sec. 6) for
+ *     R(omega) = -J(psi, omega) + D Delta_h omega,
+ * the first two steps being classical RK4 steps of the same dt; each Poisson solve starts
+ * from the extrapolation 2 psi^k - psi^{k-1} of the last two solutions (Sec. 6).
+ * Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_CUDA.
+ */
+int dg_sim_create(dg_sim** s, dg_grid* g, double D, double dt, int precision, double cg_tol,
+                  int cg_maxit, const double* omega0, void* stream);
+int dg_sim_destroy(dg_sim* s);
+
+/* dg_step -- advance nsteps >= 0 time steps (asynchronous; solver errors are recorded in
+ * the simulation and reported by dg_sim_status). */
+int dg_step(dg_sim* s, int nsteps, void* stream);
+
+/* dg_sim_status -- synchronises the stream and fills info; returns info->status. */
+int dg_sim_status(dg_sim* s, dg_sim_info* info, void* stream);
+
+/* dg_sim_get -- copies the current omega and psi (device pointers, either may be NULL). */
+int dg_sim_get(dg_sim* s, double* omega, double* psi, void* stream);
+
+/*
+ * dg_sim_get_state / dg_sim_set_state -- the full stepper state (device pointers, all
+ * required): omega^k, psi^k, psi^{k-1}, R^{k-1}, R^{k-2} and the step index k.  Setting the
+ * state lets a caller (e.g. a checkpoint or a parity test) resume bit-exactly.  For
+ * DG_MIXED the R history is stored in float32 and is converted on get/set.
+ */
+int dg_sim_get_state(dg_sim* s, long long* step, double* omega, double* psi, double* psi_prev,
+                     double* R1, double* R2, void* stream);
+int dg_sim_set_state(dg_sim* s, long long step, const double* omega, const double* psi,
+                     const double* psi_prev, const double* R1, const double* R2, void* stream);
+
+/* dg_sim_invariants -- (V, E, Omega) of the current state; synchronises the stream. */
+int dg_sim_invariants(dg_sim* s, double out[3], void* stream);
+
+/*
+ * dg_sim_set_cg -- change the Poisson solver controls of later steps: tolerance tol > 0,
+ * iteration cap maxit >= 1 and, if fixed_iters > 0, exactly that many CG iterations per
+ * solve (parity mode: two implementations then take the same Krylov steps, Sec. 6).
+ */
+int dg_sim_set_cg(dg_sim* s, double tol, int maxit, int fixed_iters);
+
+/*
+ * dg_sim_set_refinement -- DG_MIXED only: each float32 inner CG sweep stops when its residual
+ * has fallen by tol_in (0 < tol_in < 1); at most max_sweeps >= 1 float64 refinement sweeps per
+ * solve (the float64 residual must reach the CG tolerance of dg_sim_create / dg_sim_set_cg).
+ */
+int dg_sim_set_refinement(dg_sim* s, double tol_in, int max_sweeps);
+
+/*
+ * dg_sim_upload / dg_sim_download -- the same state transfers with HOST pointers (pinned or
+ * pageable), copied by the library on the stream.  upload takes the full stepper state of
+ * dg_sim_set_state; download returns omega and psi (either may be NULL) and synchronises.
+ */
+int dg_sim_upload(dg_sim* s, long long step, const double* omega, const double* psi, const double* psi_prev,
+                  const double* R1, const double* R2, void* stream);
+int dg_sim_download(dg_sim* s, double* omega, double* psi, void* stream);
+
+/* ---- launch accounting and device timing of the hot kernels ------------------------ */
+typedef struct {
+  long long launches;      /* kernels this simulation launched since the last reset        */
+  long long rhs_launches;  /* right-hand-side kernels (bracket + viscous term + update)     */
+  long long cg_launches;   /* persistent Poisson-solve kernels                              */
+  double rhs_ms;           /* summed device time of the RHS launches (timing enabled)       */
+  double cg_ms;            /* summed device time of the solve launches (timing enabled)     */
+} dg_sim_counters;
+
+/* Reset the counters; enable != 0 also brackets every RHS / solve launch with CUDA events on
+ * the launching stream (read back by dg_sim_get_counters, which synchronises the stream). */
+int dg_sim_set_timing(dg_sim* s, int enable);
+int dg_sim_get_counters(dg_sim* s, dg_sim_counters* c, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGK_DG_H */

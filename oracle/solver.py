@@ -22,10 +22,14 @@ import numpy as np
 
 
 def poisson_rhs(ops, omega):
-    """b = W (omega - mean_W omega)."""
+    """b = W (omega - mean_W omega).  The mean is evaluated in two passes (the mean of the
+    first-pass deviations corrects the first pass), so that b has no rounding-sized component
+    along the constants, the kernel of A."""
     W = ops.W2
-    mean = float(np.sum(W * omega)) / float(np.sum(W))
-    return W * (omega - mean)
+    sW = float(np.sum(W))
+    m1 = float(np.sum(W * omega)) / sW
+    m2 = float(np.sum(W * (omega - m1))) / sW
+    return W * (omega - (m1 + m2))
 
 
 MAX_RESTARTS = 20

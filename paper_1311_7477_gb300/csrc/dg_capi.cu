@@ -1,0 +1,1005 @@
+// The C ABI of libdgk (include/dg.h): handles, argument checks, operator tables, kernel
+// launches and the time-stepper orchestration.  No function here aborts or prints; errors
+// are returned as DG_ERR_* with a thread-local message.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_kernels.cuh"
+#include "dg_tables.h"
+
+using namespace dgk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(e_ == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA, \
+                                       "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+// Host copies of the device operator tables for one n, in float64 and float32.
+struct OpsHost {
+  alignas(16) unsigned char d[sizeof(Ops2D<double, kMaxN>)];
+  alignas(16) unsigned char f[sizeof(Ops2D<float, kMaxN>)];
+};
+
+template <typename T, int N>
+void fill_op(Op1D<T, N>& o, const double M[kMaxN][kMaxN], const double* a, const double* r, const double* d,
+             const double* s) {
+  for (int i = 0; i < N; ++i) {
+    for (int j = 0; j < N; ++j) o.M[i][j] = T(M[i][j]);
+    o.a[i] = T(a[i]);
+    o.r[i] = T(r[i]);
+    o.d[i] = T(d[i]);
+    o.s[i] = T(s[i]);
+  }
+}
+
+// Builds the 2D operator tables from the dimensionless per-n tables (Sec. 4.2 / Sec. 6):
+//   d/dx   = C0/hx, lifts muR/hx and -muL/hx on the traces lL . u_{c+1}, lR . u_{c-1};
+//   -Delta = W^-1 A (x-part: w^-1 A1cc / hx^2, w^-1 betaA / hx^2 on lL . u_{c+1},
+//            w^-1 lL / hx^2 on betaA . u_{c-1});
+//   W^-1/2 A W^-1/2 = the same with w^-1/2 on both sides.
+template <typename T, int N>
+Ops2D<T, N> make_ops(const RefTables& t, double hx, double hy) {
+  Ops2D<T, N> O;
+  double wh[kMaxN], rw[kMaxN];
+  for (int j = 0; j < N; ++j) {
+    wh[j] = 0.5 * t.w[j];
+    rw[j] = 1.0 / std::sqrt(wh[j]);
+  }
+  const double hs[2] = {hx, hy};
+  for (int dir = 0; dir < 2; ++dir) {
+    const double h = hs[dir], h2 = h * h;
+    double M[kMaxN][kMaxN], a[kMaxN], r[kMaxN], d[kMaxN], s[kMaxN];
+    // central derivative
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) M[i][j] = t.C0[i][j] / h;
+      a[i] = t.muR[i] / h;
+      r[i] = t.lL[i];
+      d[i] = -t.muL[i] / h;
+      s[i] = t.lR[i];
+    }
+    fill_op<T, N>(dir == 0 ? O.dx : O.dy, M, a, r, d, s);
+    // symmetrically scaled LDG stiffness
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) M[i][j] = rw[i] * t.A1cc[i][j] * rw[j] / h2;
+      a[i] = rw[i] * t.betaA[i] / h2;
+      r[i] = rw[i] * t.lL[i];
+      d[i] = rw[i] * t.lL[i] / h2;
+      s[i] = rw[i] * t.betaA[i];
+    }
+    fill_op<T, N>(dir == 0 ? O.kx : O.ky, M, a, r, d, s);
+    // -Delta_h = W^-1 A
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) M[i][j] = t.A1cc[i][j] / (wh[i] * h2);
+      a[i] = t.betaA[i] / (wh[i] * h2);
+      r[i] = t.lL[i];
+      d[i] = t.lL[i] / (wh[i] * h2);
+      s[i] = t.betaA[i];
+    }
+    fill_op<T, N>(dir == 0 ? O.lx : O.ly, M, a, r, d, s);
+  }
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double w = (hy * wh[a]) * (hx * wh[b]);
+      O.wq[a * N + b] = T(w);
+      O.sw[a * N + b] = T(std::sqrt(w));
+      O.isw[a * N + b] = T(1.0 / std::sqrt(w));
+    }
+  return O;
+}
+
+template <int N>
+NodeWeights<N> make_weights(const RefTables& t, double hx, double hy) {
+  NodeWeights<N> W;
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double w = (hy * 0.5 * t.w[a]) * (hx * 0.5 * t.w[b]);
+      W.w[a * N + b] = w;
+      W.sw[a * N + b] = std::sqrt(w);
+      W.isw[a * N + b] = 1.0 / std::sqrt(w);
+    }
+  return W;
+}
+
+// Built-in tiles (cells per block, TY x TX) for the RHS kernel and the CG kernel.
+void default_tiles(int n, int& rty, int& rtx, int& cty, int& ctx) {
+  static const int R[6][2] = {{0, 0}, {16, 16}, {8, 16}, {8, 8}, {4, 8}, {4, 8}};
+  static const int Cg[6][2] = {{0, 0}, {16, 16}, {16, 16}, {8, 16}, {8, 8}, {8, 8}};
+  rty = R[n][0];
+  rtx = R[n][1];
+  cty = Cg[n][0];
+  ctx = Cg[n][1];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------------------
+
+struct Workspace {
+  size_t ndof = 0;
+  int grid_cap = 0;  // capacity of the partials (blocks)
+  double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *y = nullptr;
+  double* part = nullptr;  // 4 * grid_cap
+  // float32 inner-solve vectors of the mixed precision path
+  float *rf = nullptr, *fr = nullptr, *fe = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fq = nullptr;
+  float* partf = nullptr;
+  SyncState* sync = nullptr;
+  SolveStatus* status = nullptr;
+  double* inv_part = nullptr;  // 3 * kInvBlocks
+  double* inv_out = nullptr;   // 3
+  double* host_out = nullptr;  // pinned 3
+};
+
+constexpr int kInvBlocks = 1024;
+
+struct dg_grid {
+  int Nx, Ny, n;
+  double Lx, Ly, hx, hy, tau;
+  RefTables rt;
+  int rTY, rTX, cTY, cTX;
+  int num_sms;
+  OpsHost ops;
+  Workspace ws;
+};
+
+struct dg_sim {
+  dg_grid* g;
+  double D, dt, tol;
+  int precision, maxit, fixed_iters;
+  long long step;
+  double* omega[2];
+  int oc;
+  double* psi[3];  // scaled: sqrt(W) psi
+  int p0, p1, p2;
+  void* R[3];      // history ring: float64 (DG_FP64) or float32 (DG_MIXED)
+  int r1, r2, rfree;
+  double *stA, *stB;  // RK stage vorticities
+  void *k2, *k3;      // RK stage slopes (same type as R)
+  double tol_in;      // inner relative tolerance of the float32 sweeps (DG_MIXED)
+  int max_sweeps;
+  Workspace ws;
+  // launch accounting / device timing
+  long long launches = 0, rhs_launches = 0, cg_launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_rhs, ev_cg;  // start/stop pairs
+  size_t n_ev_rhs = 0, n_ev_cg = 0;
+};
+
+namespace {
+
+void free_ws(Workspace& w) {
+  cudaFree(w.r);
+  cudaFree(w.p0);
+  cudaFree(w.p1);
+  cudaFree(w.q);
+  cudaFree(w.y);
+  cudaFree(w.part);
+  cudaFree(w.sync);
+  cudaFree(w.status);
+  cudaFree(w.inv_part);
+  cudaFree(w.inv_out);
+  cudaFree(w.rf);
+  cudaFree(w.fr);
+  cudaFree(w.fe);
+  cudaFree(w.fp0);
+  cudaFree(w.fp1);
+  cudaFree(w.fq);
+  cudaFree(w.partf);
+  if (w.host_out) cudaFreeHost(w.host_out);
+  w = Workspace{};
+}
+
+int alloc_ws(Workspace& w, size_t ndof, int grid_cap, bool with_y) {
+  w.ndof = ndof;
+  w.grid_cap = grid_cap;
+  const size_t bytes = ndof * sizeof(double);
+  CUDA_TRY(cudaMalloc(&w.r, bytes));
+  CUDA_TRY(cudaMalloc(&w.p0, bytes));
+  CUDA_TRY(cudaMalloc(&w.p1, bytes));
+  CUDA_TRY(cudaMalloc(&w.q, bytes));
+  if (with_y) CUDA_TRY(cudaMalloc(&w.y, bytes));
+  CUDA_TRY(cudaMalloc(&w.part, 4 * (size_t)grid_cap * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.sync, sizeof(SyncState)));
+  CUDA_TRY(cudaMalloc(&w.status, sizeof(SolveStatus)));
+  CUDA_TRY(cudaMemset(w.sync, 0, sizeof(SyncState)));
+  CUDA_TRY(cudaMemset(w.status, 0, sizeof(SolveStatus)));
+  CUDA_TRY(cudaMalloc(&w.inv_part, 3 * (size_t)kInvBlocks * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.inv_out, 3 * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&w.host_out, 3 * sizeof(double)));
+  return DG_OK;
+}
+
+int alloc_ws_mixed(Workspace& w) {
+  const size_t fb = w.ndof * sizeof(float);
+  CUDA_TRY(cudaMalloc(&w.rf, fb));
+  CUDA_TRY(cudaMalloc(&w.fr, fb));
+  CUDA_TRY(cudaMalloc(&w.fe, fb));
+  CUDA_TRY(cudaMalloc(&w.fp0, fb));
+  CUDA_TRY(cudaMalloc(&w.fp1, fb));
+  CUDA_TRY(cudaMalloc(&w.fq, fb));
+  CUDA_TRY(cudaMalloc(&w.partf, 4 * (size_t)w.grid_cap * sizeof(float)));
+  return DG_OK;
+}
+
+size_t ndof_of(const dg_grid* g) { return (size_t)g->Nx * g->Ny * g->n * g->n; }
+
+Geom geom_of(const dg_grid* g, int TY, int TX) {
+  Geom G;
+  G.Nx = g->Nx;
+  G.Ny = g->Ny;
+  G.TY = std::min(TY, g->Ny);
+  G.TX = std::min(TX, g->Nx);
+  G.tilesX = (g->Nx + G.TX - 1) / G.TX;
+  G.tilesY = (g->Ny + G.TY - 1) / G.TY;
+  return G;
+}
+
+template <typename T, int N>
+const Ops2D<T, N>& ops_of(const dg_grid* g) {
+  if constexpr (sizeof(T) == 8) return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.d);
+  else return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.f);
+}
+
+template <int N>
+void build_ops(dg_grid* g) {
+  new (g->ops.d) Ops2D<double, N>(make_ops<double, N>(g->rt, g->hx, g->hy));
+  new (g->ops.f) Ops2D<float, N>(make_ops<float, N>(g->rt, g->hx, g->hy));
+}
+
+template <class F>
+int dispatch_n(int n, F&& f) {
+  switch (n) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+  }
+  return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
+}
+
+template <typename Kern>
+int set_smem(Kern k, size_t bytes) {
+  if (bytes > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return DG_OK;
+}
+
+// ---- launches ---------------------------------------------------------------------------
+
+template <typename T, int N>
+int launch_rhs(const dg_grid* g, const RhsArgs<T>& A, cudaStream_t st) {
+  const Geom G = geom_of(g, g->rTY, g->rTX);
+  const size_t smem = rhs_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  if (int rc = set_smem(rhs_kernel<T, N>, smem)) return rc;
+  rhs_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, A);
+  CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+template <typename T, int N>
+int launch_apply(const dg_grid* g, const double* x, double* y, int mode, cudaStream_t st) {
+  const Geom G = geom_of(g, g->cTY, g->cTX);
+  const size_t smem = apply_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  if (int rc = set_smem(apply_kernel<T, N>, smem)) return rc;
+  apply_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, x, y, mode);
+  CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+// Cooperative launch of the persistent CG kernel: as many blocks as can be co-resident
+// (capped by the number of tiles and the partials capacity).
+// Records the next event of a start/stop pool (growing it as needed).
+int record_event(std::vector<cudaEvent_t>& pool, size_t& used, cudaStream_t st) {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    pool.push_back(e);
+  }
+  CUDA_TRY(cudaEventRecord(pool[used++], st));
+  return DG_OK;
+}
+
+template <typename T, int N>
+int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
+  const Geom G = geom_of(g, g->cTY, g->cTX);
+  const size_t smem = cg_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  auto kern = cg_kernel<T, N>;
+  if (int rc = set_smem(kern, smem)) return rc;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  if (per_sm < 1) return fail(DG_ERR_CUDA, "CG kernel does not fit on an SM (smem %zu B)", smem);
+  int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
+  grid = std::min(grid, w.grid_cap);
+  A.part = reinterpret_cast<T*>(w.part);
+  A.sync = w.sync;
+  A.status = w.status;
+  CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
+  void* args[] = {(void*)&ops_of<T, N>(g), (void*)&G, (void*)&A};
+  const bool tm = timed && timed->timing;
+  if (tm)
+    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem, st));
+  if (tm)
+    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
+  return DG_OK;
+}
+
+template <int N>
+int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
+  const Geom G = geom_of(g, g->cTY, g->cTX);
+  const size_t smem = mixed_smem_bytes<N>(G.TY, G.TX);
+  auto kern = mixed_cg_kernel<N>;
+  if (int rc = set_smem(kern, smem)) return rc;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  if (per_sm < 1) return fail(DG_ERR_CUDA, "mixed CG kernel does not fit on an SM (smem %zu B)", smem);
+  int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
+  grid = std::min(grid, w.grid_cap);
+  A.rf = w.rf;
+  A.v = CgVectors<float>{w.fe, w.fr, w.fp0, w.fp1, w.fq};
+  A.partd = w.part;
+  A.partf = w.partf;
+  A.sync = w.sync;
+  A.status = w.status;
+  CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
+  void* args[] = {(void*)&ops_of<double, N>(g), (void*)&ops_of<float, N>(g), (void*)&G, (void*)&A};
+  const bool tm = timed && timed->timing;
+  if (tm)
+    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem, st));
+  if (tm)
+    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
+  return DG_OK;
+}
+
+int read_status(const Workspace& w, SolveStatus* out, cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(out, w.status, sizeof(SolveStatus), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+int flags_to_status(int flags) {
+  if (flags & kFlagTimeout) return fail(DG_ERR_TIMEOUT, "a device-side wait hit its cap");
+  if (flags & kFlagBreakdown) return fail(DG_ERR_NONFINITE, "CG breakdown (p.q not positive or not finite)");
+  if (flags & kFlagNoconv) return fail(DG_ERR_NOCONV, "CG reached maxit before the tolerance");
+  return DG_OK;
+}
+
+template <int N>
+int launch_invariants(const dg_grid* g, const double* psi, const double* omega, int psi_scaled, const Workspace& w,
+                      cudaStream_t st) {
+  const NodeWeights<N> W = make_weights<N>(g->rt, g->hx, g->hy);
+  const size_t nd = ndof_of(g);
+  const int blocks = (int)std::min<size_t>(kInvBlocks, (nd + kThreads - 1) / kThreads);
+  invariants_partial_kernel<N><<<blocks, kThreads, 0, st>>>(W, psi, omega, nd, psi_scaled, w.inv_part);
+  invariants_final_kernel<<<1, 32, 0, st>>>(w.inv_part, blocks, w.inv_out);
+  CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int finish_invariants(const Workspace& w, double out[3], cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(w.host_out, w.inv_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int j = 0; j < 3; ++j) out[j] = w.host_out[j];
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(out[j])) return fail(DG_ERR_NONFINITE, "invariant %d is not finite", j);
+  return DG_OK;
+}
+
+int co_resident_cap(const dg_grid* g) { return std::max(64, 8 * g->num_sms); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err; }
+
+int dg_version(void) { return 100; }
+
+int dg_ref_tables_len(int n) { return (n >= 1 && n <= kMaxN) ? 7 * n + 2 * n * n : 0; }
+
+int dg_ref_tables(int n, double tau, double* out, int out_len) {
+  if (n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
+  if (!(tau >= 0.0)) return fail(DG_ERR_ARG, "tau must be >= 0");
+  if (!out || out_len < dg_ref_tables_len(n)) return fail(DG_ERR_ARG, "output buffer too small");
+  RefTables t;
+  if (build_ref_tables(n, tau, &t)) return fail(DG_ERR_ARG, "table construction failed");
+  double* o = out;
+  for (int i = 0; i < n; ++i) *o++ = t.x[i];
+  for (int i = 0; i < n; ++i) *o++ = t.w[i];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) *o++ = t.C0[i][j];
+  for (int i = 0; i < n; ++i) *o++ = t.muR[i];
+  for (int i = 0; i < n; ++i) *o++ = t.muL[i];
+  for (int i = 0; i < n; ++i) *o++ = t.lL[i];
+  for (int i = 0; i < n; ++i) *o++ = t.lR[i];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) *o++ = t.A1cc[i][j];
+  for (int i = 0; i < n; ++i) *o++ = t.betaA[i];
+  return DG_OK;
+}
+
+int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, double tau) {
+  if (!gp) return fail(DG_ERR_ARG, "g is NULL");
+  *gp = nullptr;
+  if (n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
+  if (Nx < 1 || Ny < 1) return fail(DG_ERR_ARG, "Nx, Ny must be >= 1");
+  if ((long long)Nx * Ny * n * n > (1ll << 31)) return fail(DG_ERR_ARG, "grid too large");
+  if (!(Lx > 0.0) || !(Ly > 0.0)) return fail(DG_ERR_ARG, "Lx, Ly must be > 0");
+  if (!(tau >= 0.0)) return fail(DG_ERR_ARG, "tau must be >= 0");
+  dg_grid* g = new (std::nothrow) dg_grid();
+  if (!g) return fail(DG_ERR_NOMEM, "host allocation failed");
+  g->Nx = Nx;
+  g->Ny = Ny;
+  g->n = n;
+  g->Lx = Lx;
+  g->Ly = Ly;
+  g->hx = Lx / Nx;
+  g->hy = Ly / Ny;
+  g->tau = tau;
+  build_ref_tables(n, tau, &g->rt);
+  default_tiles(n, g->rTY, g->rTX, g->cTY, g->cTX);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete g;
+    return fail(DG_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  dispatch_n(n, [&](auto nc) {
+    build_ops<decltype(nc)::value>(g);
+    return DG_OK;
+  });
+  if (int rc = alloc_ws(g->ws, ndof_of(g), co_resident_cap(g), true)) {
+    free_ws(g->ws);
+    delete g;
+    return rc;
+  }
+  *gp = g;
+  return DG_OK;
+}
+
+int dg_grid_destroy(dg_grid* g) {
+  if (!g) return DG_OK;
+  free_ws(g->ws);
+  delete g;
+  return DG_OK;
+}
+
+long long dg_grid_dof(const dg_grid* g) { return g ? (long long)ndof_of(g) : 0; }
+
+int dg_grid_nodes(const dg_grid* g, double* xn, double* yn, double* w) {
+  if (!g) return fail(DG_ERR_ARG, "g is NULL");
+  const int n = g->n;
+  if (xn)
+    for (int c = 0; c < g->Nx; ++c)
+      for (int b = 0; b < n; ++b) xn[c * n + b] = (c + 0.5) * g->hx + 0.5 * g->hx * g->rt.x[b];
+  if (yn)
+    for (int c = 0; c < g->Ny; ++c)
+      for (int a = 0; a < n; ++a) yn[c * n + a] = (c + 0.5) * g->hy + 0.5 * g->hy * g->rt.x[a];
+  if (w)
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) w[a * n + b] = (g->hy * 0.5 * g->rt.w[a]) * (g->hx * 0.5 * g->rt.w[b]);
+  return DG_OK;
+}
+
+int dg_grid_set_tiles(dg_grid* g, int TY, int TX) {
+  if (!g) return fail(DG_ERR_ARG, "g is NULL");
+  if (TY == 0 && TX == 0) {
+    default_tiles(g->n, g->rTY, g->rTX, g->cTY, g->cTX);
+    return DG_OK;
+  }
+  if (TY < 1 || TX < 1 || TY > 64 || TX > 64) return fail(DG_ERR_ARG, "tile must be 1..64 cells per side");
+  const size_t rs = (size_t)(TY + 2) * (TX + 2) * (7 * g->n * g->n + 12 * g->n) * sizeof(double);
+  if (rs > 200 * 1024) return fail(DG_ERR_ARG, "tile %dx%d needs %zu B of shared memory", TY, TX, rs);
+  g->rTY = g->cTY = TY;
+  g->rTX = g->cTX = TX;
+  return DG_OK;
+}
+
+int dg_bracket(dg_grid* g, const double* psi, const double* omega, double* J, void* stream) {
+  if (!g || !psi || !omega || !J) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(psi) || !aligned8(omega) || !aligned8(J)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (J == psi || J == omega) return fail(DG_ERR_ARG, "J must not alias psi or omega");
+  RhsArgs<double> A{};
+  A.psi = psi;
+  A.omega_in = omega;
+  A.omega_base = omega;
+  A.omega_out = J;
+  A.bracket_only = 1;
+  return dispatch_n(g->n, [&](auto nc) { return launch_rhs<double, decltype(nc)::value>(g, A, as_stream(stream)); });
+}
+
+int dg_laplace_apply(dg_grid* g, const double* x, double* y, int mode, void* stream) {
+  if (!g || !x || !y) return fail(DG_ERR_ARG, "NULL argument");
+  if (mode != 0 && mode != 1) return fail(DG_ERR_ARG, "mode must be 0 (A x) or 1 (Delta_h x)");
+  if (!aligned8(x) || !aligned8(y)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (x == y) return fail(DG_ERR_ARG, "y must not alias x");
+  return dispatch_n(g->n,
+                    [&](auto nc) { return launch_apply<double, decltype(nc)::value>(g, x, y, mode, as_stream(stream)); });
+}
+
+int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, int maxit, int fixed_iters,
+                     int* iters, double* relres, void* stream) {
+  if (!g || !omega || !psi) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(omega) || !aligned8(psi)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (maxit < 0 || fixed_iters < 0) return fail(DG_ERR_ARG, "maxit and fixed_iters must be >= 0");
+  if (fixed_iters == 0 && !(tol > 0.0)) return fail(DG_ERR_ARG, "tol must be > 0");
+  cudaStream_t st = as_stream(stream);
+  CgArgs<double> A{};
+  A.omega = omega;
+  A.xa = psi;
+  A.ca = 1.0;
+  A.x_unscaled = 1;
+  A.v = CgVectors<double>{g->ws.y, g->ws.r, g->ws.p0, g->ws.p1, g->ws.q};
+  A.psi_out = psi;
+  A.tol2 = tol * tol;
+  A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
+  A.fixed_iters = fixed_iters;
+  A.sumW = g->Lx * g->Ly;
+  int rc = dispatch_n(g->n, [&](auto nc) { return launch_cg<double, decltype(nc)::value>(g, A, g->ws, st); });
+  if (rc) return rc;
+  SolveStatus s;
+  if ((rc = read_status(g->ws, &s, st))) return rc;
+  if (iters) *iters = s.last_iters;
+  if (relres) *relres = s.last_rhob > 0 ? std::sqrt(std::max(s.last_rho, 0.0) / s.last_rhob) : 0.0;
+  return flags_to_status(s.last_flags);
+}
+
+int dg_invariants(dg_grid* g, const double* psi, const double* omega, double out[3], void* stream) {
+  if (!g || !psi || !omega || !out) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  int rc = dispatch_n(g->n, [&](auto nc) {
+    return launch_invariants<decltype(nc)::value>(g, psi, omega, 0, g->ws, st);
+  });
+  if (rc) return rc;
+  return finish_invariants(g->ws, out, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Simulations
+// ---------------------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+void free_events(dg_sim* s) {
+  for (auto e : s->ev_rhs) cudaEventDestroy(e);
+  for (auto e : s->ev_cg) cudaEventDestroy(e);
+  s->ev_rhs.clear();
+  s->ev_cg.clear();
+  s->n_ev_rhs = s->n_ev_cg = 0;
+}
+
+void free_sim(dg_sim* s) {
+  free_events(s);
+  for (auto& p : s->omega) cudaFree(p);
+  for (auto& p : s->psi) cudaFree(p);
+  for (auto& p : s->R) cudaFree(p);
+  cudaFree(s->stA);
+  cudaFree(s->stB);
+  cudaFree(s->k2);
+  cudaFree(s->k3);
+  free_ws(s->ws);
+}
+
+// Poisson solve inside the stepper: y = solve(omega) from y0 = ca xa + cb xb (scaled space):
+// the persistent float64 CG kernel, or (DG_MIXED) the float64-residual / float32-CG
+// refinement kernel.
+int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const double* xb, double cb, double* y,
+              cudaStream_t st) {
+  dg_grid* g = s->g;
+  int rc;
+  if (s->precision == DG_MIXED) {
+    MixedArgs A{};
+    A.omega = omega;
+    A.xa = xa;
+    A.xb = xb;
+    A.ca = ca;
+    A.cb = cb;
+    A.x_unscaled = 0;
+    A.y = y;
+    A.tol2 = s->tol * s->tol;
+    A.tol_in2 = s->tol_in * s->tol_in;
+    A.max_sweeps = s->max_sweeps;
+    A.maxit_in = s->maxit;
+    A.sumW = g->Lx * g->Ly;
+    rc = dispatch_n(g->n, [&](auto nc) { return launch_mixed<decltype(nc)::value>(g, A, s->ws, st, s); });
+  } else {
+    CgArgs<double> A{};
+    A.omega = omega;
+    A.xa = xa;
+    A.xb = xb;
+    A.ca = ca;
+    A.cb = cb;
+    A.x_unscaled = 0;
+    A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
+    A.tol2 = s->tol * s->tol;
+    A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
+    A.fixed_iters = s->fixed_iters;
+    A.sumW = g->Lx * g->Ly;
+    rc = dispatch_n(g->n, [&](auto nc) { return launch_cg<double, decltype(nc)::value>(g, A, s->ws, st, s); });
+  }
+  if (!rc) {
+    s->launches += 1;
+    s->cg_launches += 1;
+  }
+  return rc;
+}
+
+// R = -J(psi, omega_in) + D Delta_h omega_in;  omega_out = omega_base + dt (c_new R + sum c_m hist_m).
+// R and the history are float64 (DG_FP64) or float32 (DG_MIXED, bracket in float32).
+template <typename T>
+int sim_rhs_t(dg_sim* s, const double* psi, const double* om_in, const double* om_base, double* om_out, void* R_out,
+              double c_new, int nhist, void* const* hist, const double* c_hist, cudaStream_t st) {
+  RhsArgs<T> A{};
+  A.psi = psi;
+  A.omega_in = om_in;
+  A.omega_base = om_base;
+  A.omega_out = om_out;
+  A.R_out = static_cast<T*>(R_out);
+  A.c_new = c_new;
+  A.nhist = nhist;
+  for (int m = 0; m < nhist; ++m) {
+    A.hist[m] = static_cast<const T*>(hist[m]);
+    A.c_hist[m] = c_hist[m];
+  }
+  A.dt = s->dt;
+  A.visc = s->D;
+  A.psi_scaled = 1;
+  return dispatch_n(s->g->n, [&](auto nc) { return launch_rhs<T, decltype(nc)::value>(s->g, A, st); });
+}
+
+int sim_rhs(dg_sim* s, const double* psi, const double* om_in, const double* om_base, double* om_out, void* R_out,
+            double c_new, int nhist, void* const* hist, const double* c_hist, cudaStream_t st) {
+  int rc;
+  if (s->timing && (rc = record_event(s->ev_rhs, s->n_ev_rhs, st))) return rc;
+  rc = (s->precision == DG_MIXED)
+           ? sim_rhs_t<float>(s, psi, om_in, om_base, om_out, R_out, c_new, nhist, hist, c_hist, st)
+           : sim_rhs_t<double>(s, psi, om_in, om_base, om_out, R_out, c_new, nhist, hist, c_hist, st);
+  if (rc) return rc;
+  if (s->timing && (rc = record_event(s->ev_rhs, s->n_ev_rhs, st))) return rc;
+  s->launches += 1;
+  s->rhs_launches += 1;
+  return DG_OK;
+}
+
+// One classical RK4 step (start-up of the multistep method).  k1 is kept as R^k.
+int sim_rk4_step(dg_sim* s, cudaStream_t st) {
+  const double* w0 = s->omega[s->oc];
+  double* w1 = s->omega[s->oc ^ 1];
+  void* k1 = s->R[s->rfree];
+  double* PA = s->psi[s->p2];
+  double* PB = s->psi[s->p1];
+  const double* P0 = s->psi[s->p0];
+  int rc;
+  if ((rc = sim_rhs(s, P0, w0, w0, s->stA, k1, 0.5, 0, nullptr, nullptr, st))) return rc;
+  if ((rc = sim_solve(s, s->stA, P0, 1.0, nullptr, 0.0, PA, st))) return rc;
+  if ((rc = sim_rhs(s, PA, s->stA, w0, s->stB, s->k2, 0.5, 0, nullptr, nullptr, st))) return rc;
+  if ((rc = sim_solve(s, s->stB, PA, 1.0, nullptr, 0.0, PB, st))) return rc;
+  if ((rc = sim_rhs(s, PB, s->stB, w0, s->stA, s->k3, 1.0, 0, nullptr, nullptr, st))) return rc;
+  if ((rc = sim_solve(s, s->stA, PB, 1.0, nullptr, 0.0, PA, st))) return rc;
+  void* const hist[3] = {k1, s->k2, s->k3};
+  const double ch[3] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0};
+  if ((rc = sim_rhs(s, PA, s->stA, w0, w1, nullptr, 1.0 / 6.0, 3, hist, ch, st))) return rc;
+  if ((rc = sim_solve(s, w1, PA, 1.0, nullptr, 0.0, PB, st))) return rc;
+  // psi^{k+1} = PB (old p1 slot), psi^k stays p0: rotate (p0, p1, p2) <- (p1, p0, p2)
+  std::swap(s->p0, s->p1);
+  // R ring: R^k = k1 (in rfree); R^{k-1} = old r1; the oldest slot becomes free
+  const int old_r1 = s->r1, old_r2 = s->r2;
+  s->r1 = s->rfree;
+  s->r2 = old_r1;
+  s->rfree = old_r2;
+  s->oc ^= 1;
+  s->step += 1;
+  return DG_OK;
+}
+
+// One AB3 step: omega^{k+1} = omega^k + dt (23 R^k - 16 R^{k-1} + 5 R^{k-2}) / 12, then the
+// Poisson solve from 2 psi^k - psi^{k-1}.
+int sim_ab3_step(dg_sim* s, cudaStream_t st) {
+  const double* w0 = s->omega[s->oc];
+  double* w1 = s->omega[s->oc ^ 1];
+  void* Rk = s->R[s->rfree];
+  void* const hist[2] = {s->R[s->r1], s->R[s->r2]};
+  const double ch[2] = {-16.0 / 12.0, 5.0 / 12.0};
+  int rc;
+  if ((rc = sim_rhs(s, s->psi[s->p0], w0, w0, w1, Rk, 23.0 / 12.0, 2, hist, ch, st))) return rc;
+  if ((rc = sim_solve(s, w1, s->psi[s->p0], 2.0, s->psi[s->p1], -1.0, s->psi[s->p2], st))) return rc;
+  const int np0 = s->p2, np1 = s->p0, np2 = s->p1;
+  s->p0 = np0;
+  s->p1 = np1;
+  s->p2 = np2;
+  const int old_r1 = s->r1, old_r2 = s->r2;
+  s->r1 = s->rfree;
+  s->r2 = old_r1;
+  s->rfree = old_r2;
+  s->oc ^= 1;
+  s->step += 1;
+  return DG_OK;
+}
+
+// History buffer <-> float64 device array (the history is float32 for DG_MIXED).
+int R_to_double(const dg_sim* s, const void* R, double* dst, cudaStream_t st) {
+  const size_t nd = ndof_of(s->g);
+  if (s->precision == DG_MIXED) {
+    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
+    convert_kernel<float, double><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(R), dst, nd);
+    CUDA_TRY(cudaGetLastError());
+    return DG_OK;
+  }
+  CUDA_TRY(cudaMemcpyAsync(dst, R, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return DG_OK;
+}
+
+int R_from_double(const dg_sim* s, const double* src, void* R, cudaStream_t st) {
+  const size_t nd = ndof_of(s->g);
+  if (s->precision == DG_MIXED) {
+    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
+    convert_kernel<double, float><<<blocks, kThreads, 0, st>>>(src, static_cast<float*>(R), nd);
+    CUDA_TRY(cudaGetLastError());
+    return DG_OK;
+  }
+  CUDA_TRY(cudaMemcpyAsync(R, src, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return DG_OK;
+}
+
+int scale_field(const dg_grid* g, const double* x, double* y, int inverse, cudaStream_t st) {
+  return dispatch_n(g->n, [&](auto nc) {
+    constexpr int N = decltype(nc)::value;
+    const NodeWeights<N> W = make_weights<N>(g->rt, g->hx, g->hy);
+    const size_t nd = ndof_of(g);
+    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
+    scale_nodes_kernel<N><<<blocks, kThreads, 0, st>>>(W, x, y, nd, inverse);
+    CUDA_TRY(cudaGetLastError());
+    return DG_OK;
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double cg_tol, int cg_maxit,
+                  const double* omega0, void* stream) {
+  if (!sp) return fail(DG_ERR_ARG, "s is NULL");
+  *sp = nullptr;
+  if (!g || !omega0) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(omega0)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (!(D >= 0.0) || !(dt > 0.0) || !(cg_tol > 0.0) || cg_maxit < 1)
+    return fail(DG_ERR_ARG, "need D >= 0, dt > 0, cg_tol > 0, cg_maxit >= 1");
+  if (precision != DG_FP64 && precision != DG_MIXED) return fail(DG_ERR_ARG, "unknown precision %d", precision);
+  cudaStream_t st = as_stream(stream);
+  dg_sim* s = new (std::nothrow) dg_sim();
+  if (!s) return fail(DG_ERR_NOMEM, "host allocation failed");
+  s->g = g;
+  s->D = D;
+  s->dt = dt;
+  s->tol = cg_tol;
+  s->maxit = cg_maxit;
+  s->precision = precision;
+  s->tol_in = 1e-4;
+  s->max_sweeps = 40;
+  s->p0 = 0;
+  s->p1 = 1;
+  s->p2 = 2;
+  s->r1 = 0;
+  s->r2 = 1;
+  s->rfree = 2;
+  const size_t bytes = ndof_of(g) * sizeof(double);
+  const size_t rbytes = ndof_of(g) * (precision == DG_MIXED ? sizeof(float) : sizeof(double));
+  auto alloc_all = [&]() -> int {
+    for (auto& p : s->omega) CUDA_TRY(cudaMalloc(&p, bytes));
+    for (auto& p : s->psi) CUDA_TRY(cudaMalloc(&p, bytes));
+    for (auto& p : s->R) CUDA_TRY(cudaMalloc(&p, rbytes));
+    CUDA_TRY(cudaMalloc(&s->stA, bytes));
+    CUDA_TRY(cudaMalloc(&s->stB, bytes));
+    CUDA_TRY(cudaMalloc(&s->k2, rbytes));
+    CUDA_TRY(cudaMalloc(&s->k3, rbytes));
+    if (int rc = alloc_ws(s->ws, ndof_of(g), co_resident_cap(g), false)) return rc;
+    return precision == DG_MIXED ? alloc_ws_mixed(s->ws) : DG_OK;
+  };
+  int rc = alloc_all();
+  if (!rc) rc = (cudaMemcpyAsync(s->omega[0], omega0, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess)
+                    ? DG_OK
+                    : fail(DG_ERR_CUDA, "copy of omega0 failed");
+  // psi^0 from a zero initial guess; psi^{-1} = psi^0 so the first extrapolation is psi^0.
+  if (!rc) rc = sim_solve(s, s->omega[0], nullptr, 0.0, nullptr, 0.0, s->psi[0], st);
+  if (!rc && cudaMemcpyAsync(s->psi[1], s->psi[0], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    rc = fail(DG_ERR_CUDA, "copy failed");
+  SolveStatus ss;
+  if (!rc) rc = read_status(s->ws, &ss, st);
+  if (!rc) rc = flags_to_status(ss.last_flags);
+  if (rc) {
+    free_sim(s);
+    delete s;
+    return rc;
+  }
+  *sp = s;
+  return DG_OK;
+}
+
+int dg_sim_destroy(dg_sim* s) {
+  if (!s) return DG_OK;
+  free_sim(s);
+  delete s;
+  return DG_OK;
+}
+
+int dg_step(dg_sim* s, int nsteps, void* stream) {
+  if (!s || nsteps < 0) return fail(DG_ERR_ARG, "bad arguments");
+  cudaStream_t st = as_stream(stream);
+  for (int i = 0; i < nsteps; ++i) {
+    const int rc = (s->step < 2) ? sim_rk4_step(s, st) : sim_ab3_step(s, st);
+    if (rc) return rc;
+  }
+  return DG_OK;
+}
+
+int dg_sim_status(dg_sim* s, dg_sim_info* info, void* stream) {
+  if (!s || !info) return fail(DG_ERR_ARG, "NULL argument");
+  SolveStatus ss;
+  if (int rc = read_status(s->ws, &ss, as_stream(stream))) return rc;
+  info->step = s->step;
+  info->cg_iters_total = ss.total_iters;
+  info->cg_iters_last = ss.last_iters;
+  info->cg_iters_max = ss.max_iters;
+  info->cg_relres_last = ss.last_rhob > 0 ? std::sqrt(std::max(ss.last_rho, 0.0) / ss.last_rhob) : 0.0;
+  info->refine_sweeps_last = ss.last_sweeps;
+  info->status = ss.flags ? flags_to_status(ss.flags) : DG_OK;
+  return info->status;
+}
+
+int dg_sim_get(dg_sim* s, double* omega, double* psi, void* stream) {
+  if (!s) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = ndof_of(s->g) * sizeof(double);
+  if (omega) CUDA_TRY(cudaMemcpyAsync(omega, s->omega[s->oc], bytes, cudaMemcpyDeviceToDevice, st));
+  if (psi) return scale_field(s->g, s->psi[s->p0], psi, 1, st);
+  return DG_OK;
+}
+
+int dg_sim_get_state(dg_sim* s, long long* step, double* omega, double* psi, double* psi_prev, double* R1, double* R2,
+                     void* stream) {
+  if (!s || !step || !omega || !psi || !psi_prev || !R1 || !R2) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = ndof_of(s->g) * sizeof(double);
+  *step = s->step;
+  CUDA_TRY(cudaMemcpyAsync(omega, s->omega[s->oc], bytes, cudaMemcpyDeviceToDevice, st));
+  if (int rc = R_to_double(s, s->R[s->r1], R1, st)) return rc;
+  if (int rc = R_to_double(s, s->R[s->r2], R2, st)) return rc;
+  if (int rc = scale_field(s->g, s->psi[s->p0], psi, 1, st)) return rc;
+  return scale_field(s->g, s->psi[s->p1], psi_prev, 1, st);
+}
+
+int dg_sim_set_state(dg_sim* s, long long step, const double* omega, const double* psi, const double* psi_prev,
+                     const double* R1, const double* R2, void* stream) {
+  if (!s || !omega || !psi || !psi_prev || !R1 || !R2 || step < 0) return fail(DG_ERR_ARG, "bad arguments");
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = ndof_of(s->g) * sizeof(double);
+  s->step = step;
+  CUDA_TRY(cudaMemcpyAsync(s->omega[s->oc], omega, bytes, cudaMemcpyDeviceToDevice, st));
+  if (int rc = R_from_double(s, R1, s->R[s->r1], st)) return rc;
+  if (int rc = R_from_double(s, R2, s->R[s->r2], st)) return rc;
+  if (int rc = scale_field(s->g, psi, s->psi[s->p0], 0, st)) return rc;
+  return scale_field(s->g, psi_prev, s->psi[s->p1], 0, st);
+}
+
+int dg_sim_set_cg(dg_sim* s, double tol, int maxit, int fixed_iters) {
+  if (!s || !(tol > 0.0) || maxit < 1 || fixed_iters < 0) return fail(DG_ERR_ARG, "bad arguments");
+  s->tol = tol;
+  s->maxit = maxit;
+  s->fixed_iters = fixed_iters;
+  return DG_OK;
+}
+
+int dg_sim_upload(dg_sim* s, long long step, const double* omega, const double* psi, const double* psi_prev,
+                  const double* R1, const double* R2, void* stream) {
+  if (!s || !omega || !psi || !psi_prev || !R1 || !R2 || step < 0) return fail(DG_ERR_ARG, "bad arguments");
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = ndof_of(s->g) * sizeof(double);
+  s->step = step;
+  CUDA_TRY(cudaMemcpyAsync(s->omega[s->oc], omega, bytes, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(s->stA, R1, bytes, cudaMemcpyHostToDevice, st));
+  if (int rc = R_from_double(s, s->stA, s->R[s->r1], st)) return rc;
+  CUDA_TRY(cudaMemcpyAsync(s->stB, R2, bytes, cudaMemcpyHostToDevice, st));
+  if (int rc = R_from_double(s, s->stB, s->R[s->r2], st)) return rc;
+  CUDA_TRY(cudaMemcpyAsync(s->stA, psi, bytes, cudaMemcpyHostToDevice, st));
+  if (int rc = scale_field(s->g, s->stA, s->psi[s->p0], 0, st)) return rc;
+  CUDA_TRY(cudaMemcpyAsync(s->stB, psi_prev, bytes, cudaMemcpyHostToDevice, st));
+  if (int rc = scale_field(s->g, s->stB, s->psi[s->p1], 0, st)) return rc;
+  return DG_OK;
+}
+
+int dg_sim_download(dg_sim* s, double* omega, double* psi, void* stream) {
+  if (!s) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = ndof_of(s->g) * sizeof(double);
+  if (omega) CUDA_TRY(cudaMemcpyAsync(omega, s->omega[s->oc], bytes, cudaMemcpyDeviceToHost, st));
+  if (psi) {
+    if (int rc = scale_field(s->g, s->psi[s->p0], s->stA, 1, st)) return rc;
+    CUDA_TRY(cudaMemcpyAsync(psi, s->stA, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+int dg_sim_set_timing(dg_sim* s, int enable) {
+  if (!s) return fail(DG_ERR_ARG, "NULL argument");
+  s->timing = enable != 0;
+  s->launches = s->rhs_launches = s->cg_launches = 0;
+  s->n_ev_rhs = s->n_ev_cg = 0;
+  return DG_OK;
+}
+
+int dg_sim_get_counters(dg_sim* s, dg_sim_counters* c, void* stream) {
+  if (!s || !c) return fail(DG_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+  c->launches = s->launches;
+  c->rhs_launches = s->rhs_launches;
+  c->cg_launches = s->cg_launches;
+  c->rhs_ms = c->cg_ms = 0.0;
+  for (size_t i = 0; i + 1 < s->n_ev_rhs; i += 2) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, s->ev_rhs[i], s->ev_rhs[i + 1]));
+    c->rhs_ms += ms;
+  }
+  for (size_t i = 0; i + 1 < s->n_ev_cg; i += 2) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, s->ev_cg[i], s->ev_cg[i + 1]));
+    c->cg_ms += ms;
+  }
+  return DG_OK;
+}
+
+int dg_sim_set_refinement(dg_sim* s, double tol_in, int max_sweeps) {
+  if (!s || !(tol_in > 0.0) || !(tol_in < 1.0) || max_sweeps < 1) return fail(DG_ERR_ARG, "bad arguments");
+  s->tol_in = tol_in;
+  s->max_sweeps = max_sweeps;
+  return DG_OK;
+}
+
+int dg_sim_invariants(dg_sim* s, double out[3], void* stream) {
+  if (!s || !out) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  int rc = dispatch_n(s->g->n, [&](auto nc) {
+    return launch_invariants<decltype(nc)::value>(s->g, s->psi[s->p0], s->omega[s->oc], 1, s->ws, st);
+  });
+  if (rc) return rc;
+  return finish_invariants(s->ws, out, st);
+}
+
+}  // extern "C"

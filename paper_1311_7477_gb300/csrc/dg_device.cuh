@@ -1,0 +1,241 @@
+// Device-side building blocks shared by the kernels: operator tables, tile geometry,
+// shared-memory tile staging, block / grid reductions and a capped grid barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dgk {
+
+// Flags a device-side solve may raise (OR-ed into the status word).
+enum : int { kFlagNoconv = 1, kFlagTimeout = 2, kFlagBreakdown = 4, kFlagNonfinite = 8 };
+
+// A 1D block-tridiagonal periodic operator whose neighbour blocks are rank one:
+//   (Op u)_c = M u_c + a (r . u_{c+1}) + d (s . u_{c-1})
+// Instances: the central-flux derivative (Sec. 4.2, Eq. discrete_der: M = C0/h,
+// a = muR/h, r = lL, d = -muL/h, s = lR), the symmetrically scaled LDG stiffness and the
+// dG Laplacian (Sec. 6).
+template <typename T, int N>
+struct Op1D {
+  T M[N][N];
+  T a[N], r[N], d[N], s[N];
+};
+
+template <typename T, int N>
+struct Ops2D {
+  Op1D<T, N> dx, dy;  // central-flux derivatives d/dx, d/dy
+  Op1D<T, N> kx, ky;  // W^-1/2 A W^-1/2 = I (x) kx + ky (x) I   (CG operator)
+  Op1D<T, N> lx, ly;  // -Delta_h = W^-1 A = lx + ly
+  T sw[N * N];        // sqrt(W_ab) per node of a cell
+  T isw[N * N];       // 1 / sqrt(W_ab)
+  T wq[N * N];        // W_ab = (hy w_a / 2)(hx w_b / 2)
+};
+
+struct Geom {
+  int Nx, Ny;          // cells
+  int TX, TY;          // tile (cells)
+  int tilesX, tilesY;
+};
+
+// One tile of cells and its one-cell halo ring in shared memory: box cell (br, bc) holds
+// grid cell (ty0 + br - 1, tx0 + bc - 1) (periodic wrap); the box row stride is BW = TX + 2.
+struct TileBox {
+  int ty0, tx0, TYe, TXe, BW;
+};
+
+__device__ __forceinline__ int wrap_index(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+__device__ __forceinline__ TileBox make_box(const Geom& G, int tile) {
+  TileBox B;
+  const int tyi = tile / G.tilesX, txi = tile - (tile / G.tilesX) * G.tilesX;
+  B.ty0 = tyi * G.TY;
+  B.tx0 = txi * G.TX;
+  B.TYe = min(G.TY, G.Ny - B.ty0);
+  B.TXe = min(G.TX, G.Nx - B.tx0);
+  B.BW = G.TX + 2;
+  return B;
+}
+
+// Stage a field into the box: load(g, k, interior) returns the value of node k of the cell
+// at global offset g (k = a*N + b).  With corners == false the four corner cells are skipped
+// (the 5-cell operators never read them).
+template <typename T, int N, class LoadF>
+__device__ __forceinline__ void stage_box(const Geom& G, const TileBox& B, T* sU, bool corners, LoadF&& load) {
+  constexpr int NN = N * N;
+  const int BWe = B.TXe + 2, BHe = B.TYe + 2;
+  const int rowlen = BWe * NN;
+  for (int br = 0; br < BHe; ++br) {
+    const bool rowhalo = (br == 0) || (br == BHe - 1);
+    const int cy = wrap_index(B.ty0 + br - 1, G.Ny);
+    const size_t rowbase = (size_t)cy * G.Nx;
+    for (int j = threadIdx.x; j < rowlen; j += blockDim.x) {
+      const int bc = j / NN;
+      const int k = j - bc * NN;
+      const bool colhalo = (bc == 0) || (bc == BWe - 1);
+      if (rowhalo && colhalo && !corners) continue;
+      const int cx = wrap_index(B.tx0 + bc - 1, G.Nx);
+      const size_t g = (rowbase + cx) * NN + k;
+      sU[(br * B.BW + bc) * NN + k] = load(g, k, !(rowhalo || colhalo));
+    }
+  }
+}
+
+// Face traces of every line of the cells an operator application needs (x-lines read from
+// sUx, y-lines from sUy, which may be the same array):
+//   x-lines (rows a) of cells ry in [0, TYe), rx in [-1, TXe]:  tXR = ox.r . row, tXL = ox.s . row
+//   y-lines (cols b) of cells ry in [-1, TYe], rx in [0, TXe):   tYR = oy.r . col, tYL = oy.s . col
+// With full == true the x-lines also cover the halo rows and the y-lines the halo columns.
+template <typename T, int N>
+__device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, const T* sUy,
+                                            const Op1D<T, N>& ox, const Op1D<T, N>& oy, T* tXR,
+                                            T* tXL, T* tYR, T* tYL, bool full) {
+  constexpr int NN = N * N;
+  const int y0 = full ? -1 : 0, y1 = full ? B.TYe + 1 : B.TYe;
+  const int x0 = full ? -1 : 0, x1 = full ? B.TXe + 1 : B.TXe;
+  const int wx = B.TXe + 2, hx = y1 - y0;   // x-line cells: rows y0..y1-1, cols -1..TXe
+  const int wy = x1 - x0, hy = B.TYe + 2;   // y-line cells: rows -1..TYe, cols x0..x1-1
+  const int nx = hx * wx * N, ny = hy * wy * N;
+  for (int i = threadIdx.x; i < nx + ny; i += blockDim.x) {
+    if (i < nx) {
+      const int c = i / N, line = i - (i / N) * N;
+      const int ry = c / wx + y0, rx = c - (c / wx) * wx - 1;
+      const int lc = (ry + 1) * B.BW + rx + 1;
+      const T* u = sUx + lc * NN + line * N;
+      T tr = T(0), tl = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        tr = fma(ox.r[j], u[j], tr);
+        tl = fma(ox.s[j], u[j], tl);
+      }
+      tXR[lc * N + line] = tr;
+      tXL[lc * N + line] = tl;
+    } else {
+      const int ii = i - nx;
+      const int c = ii / N, line = ii - (ii / N) * N;
+      const int ry = c / wy - 1, rx = c - (c / wy) * wy + x0;
+      const int lc = (ry + 1) * B.BW + rx + 1;
+      const T* u = sUy + lc * NN + line;
+      T tr = T(0), tl = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        tr = fma(oy.r[j], u[j * N], tr);
+        tl = fma(oy.s[j], u[j * N], tl);
+      }
+      tYR[lc * N + line] = tr;
+      tYL[lc * N + line] = tl;
+    }
+  }
+}
+
+// (Op_x u) at node (a, b) of box cell lc, using the staged field and its x-line traces.
+template <typename T, int N>
+__device__ __forceinline__ T op_x_at(const T* sU, const T* tXR, const T* tXL, const Op1D<T, N>& o,
+                                     int lc, int a, int b) {
+  const T* u = sU + lc * (N * N) + a * N;
+  T acc = o.a[b] * tXR[(lc + 1) * N + a];
+  acc = fma(o.d[b], tXL[(lc - 1) * N + a], acc);
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc = fma(o.M[b][j], u[j], acc);
+  return acc;
+}
+
+// (Op_y u) at node (a, b) of box cell lc (the c+1 neighbour in y is one box row up).
+template <typename T, int N>
+__device__ __forceinline__ T op_y_at(const T* sU, const T* tYR, const T* tYL, const Op1D<T, N>& o,
+                                     int lc, int BW, int a, int b) {
+  const T* u = sU + lc * (N * N) + b;
+  T acc = o.a[a] * tYR[(lc + BW) * N + b];
+  acc = fma(o.d[a], tYL[(lc - BW) * N + b], acc);
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc = fma(o.M[a][j], u[j * N], acc);
+  return acc;
+}
+
+// ---- reductions ------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_down(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum; the result is valid in thread 0.  red: >= 32 values of scratch.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  v = warp_sum_down(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T t = T(0);
+  if (w == 0) {
+    t = (l < (int)(blockDim.x >> 5)) ? red[l] : T(0);
+    t = warp_sum_down(t);
+  }
+  return t;
+}
+
+// Sum of G per-block partials p[i*stride], in a fixed order, returned to every thread.
+// Every block computes the bit-identical value.  Reads bypass L1 (written by other blocks).
+template <typename T>
+__device__ __forceinline__ T sum_partials(const T* p, int G, int stride, T* bcast) {
+  if (threadIdx.x < 32) {
+    T v = T(0);
+    for (int i = threadIdx.x; i < G; i += 32) v += __ldcg(p + (size_t)i * stride);
+    v = warp_sum_down(v);
+    if (threadIdx.x == 0) *bcast = v;
+  }
+  __syncthreads();
+  const T r = *bcast;
+  __syncthreads();
+  return r;
+}
+
+// ---- grid barrier for persistent cooperative kernels -----------------------------------
+
+struct SyncState {
+  unsigned int count;
+  unsigned int gen;
+  int error;
+  int pad;
+};
+
+// Waits of a block at the barrier give up after this many polls (~1 s with the sleep
+// below) and raise kFlagTimeout; every later barrier then returns false at once.
+constexpr unsigned long long kSpinCap = 1ull << 23;
+
+// All blocks of a cooperative launch meet here.  Returns false if any block raised an error.
+__device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &s->gen;
+    volatile int* verr = &s->error;
+    const unsigned int gen0 = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&s->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&s->count, 0u);
+      __threadfence();
+      atomicAdd(&s->gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == gen0) {
+        if (*verr) break;
+        if (++spins > kSpinCap) {
+          atomicCAS(&s->error, 0, kFlagTimeout);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    *s_flag = *verr;
+  }
+  __syncthreads();
+  return *s_flag == 0;
+}
+
+}  // namespace dgk

@@ -1,0 +1,763 @@
+// The hot-path kernels, templated on the arithmetic type T (double or float) and the
+// number of nodes per cell and dimension N (1..5).
+//
+//   rhs_kernel       bracket J(psi, omega) (Eq. J) + viscous term + multistep update, fused
+//   apply_kernel     the LDG operator A or Delta_h on a field
+//   cg_kernel        persistent cooperative conjugate-gradient Poisson solve (Sec. 6)
+//   mixed_cg_kernel  float64 residual / float32 inner CG iterative refinement
+//   invariants_*     V, E, Omega by quadrature (Eq. quantities, Eq. def_norm)
+#pragma once
+
+#include "dg_device.cuh"
+
+namespace dgk {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+// a*b - c*d with both products rounded separately (never contracted into an FMA), so that
+// the bracket's antisymmetry J(f, g) = -J(g, f) and J(f, f) = 0 hold bitwise.
+template <typename T>
+__device__ __forceinline__ T prod_diff(T a, T b, T c, T d) {
+  return sub_rn(mul_rn(a, b), mul_rn(c, d));
+}
+
+// =========================================================================================
+// Right-hand side: R = -J(psi, omega) + D Delta_h omega and the update
+//   omega_out = omega_base + dt (c_new R + sum_m c_hist[m] hist[m])
+// (AB3: c = 23/12, -16/12, 5/12; the RK4 start-up stages use other coefficients).
+// One thread block per tile of TY x TX cells; the tile and a one-cell halo ring (corners
+// included: the second derivatives of J+x and Jx+ reach the diagonal neighbours) are staged
+// in shared memory, all intermediate products stay there.
+// =========================================================================================
+template <typename T>
+struct RhsArgs {
+  const double* psi;        // stream function; times sqrt(W) if psi_scaled
+  const double* omega_in;   // vorticity at which R is evaluated (halo reads)
+  const double* omega_base; // omega^k of the update (own nodes only; may alias omega_out)
+  double* omega_out;        // updated vorticity, or J in bracket-only mode
+  T* R_out;                 // fresh R (may alias one hist buffer); may be null
+  const T* hist[3];
+  double c_new;
+  double c_hist[3];
+  int nhist;
+  double dt;
+  double visc;
+  int psi_scaled;
+  int bracket_only;
+};
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t rhs_smem_values(int TY, int TX) {
+  return (size_t)(TY + 2) * (TX + 2) * (7 * N * N + 12 * N);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+                                                      const __grid_constant__ RhsArgs<T> A) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const TileBox B = make_box(G, blockIdx.x);
+  const int boxc = (G.TY + 2) * (G.TX + 2);
+  T* sPsi = sm;
+  T* sOm = sPsi + boxc * NN;
+  T* sFx = sOm + boxc * NN;  // f_x, later h2 = f_x g - f g_x   (cells with rx in [0,TXe))
+  T* sGx = sFx + boxc * NN;
+  T* sFy = sGx + boxc * NN;  // f_y, later h1 = f g_y - f_y g   (cells with ry in [0,TYe))
+  T* sGy = sFy + boxc * NN;
+  T* sJ = sGy + boxc * NN;   // J++ on the tile
+  T* t0 = sJ + boxc * NN;
+  T *tPxR = t0, *tPxL = t0 + boxc * N, *tPyR = t0 + 2 * boxc * N, *tPyL = t0 + 3 * boxc * N;
+  T *tOxR = t0 + 4 * boxc * N, *tOxL = t0 + 5 * boxc * N, *tOyR = t0 + 6 * boxc * N, *tOyL = t0 + 7 * boxc * N;
+  T *tLxR = t0 + 8 * boxc * N, *tLxL = t0 + 9 * boxc * N, *tLyR = t0 + 10 * boxc * N, *tLyL = t0 + 11 * boxc * N;
+  const int BW = B.BW;
+
+  // S0: stage psi and omega on the tile with its full halo ring.
+  stage_box<T, N>(G, B, sPsi, true, [&](size_t g, int k, bool) {
+    const double v = A.psi[g];
+    return A.psi_scaled ? T(v) * C.isw[k] : T(v);
+  });
+  stage_box<T, N>(G, B, sOm, true, [&](size_t g, int, bool) { return T(A.omega_in[g]); });
+  __syncthreads();
+
+  // S1: face traces for the first derivatives (every staged cell) and the viscous term.
+  line_traces<T, N>(B, sPsi, sPsi, C.dx, C.dy, tPxR, tPxL, tPyR, tPyL, true);
+  line_traces<T, N>(B, sOm, sOm, C.dx, C.dy, tOxR, tOxL, tOyR, tOyL, true);
+  if (A.visc != 0.0) line_traces<T, N>(B, sOm, sOm, C.lx, C.ly, tLxR, tLxL, tLyR, tLyL, false);
+  __syncthreads();
+
+  // S2: f_x, g_x on rows [-1, TYe] x cols [0, TXe); f_y, g_y on rows [0, TYe) x cols [-1, TXe].
+  {
+    const int n1 = (B.TYe + 2) * B.TXe * NN;
+    const int n2 = B.TYe * (B.TXe + 2) * NN;
+    for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+      if (i < n1) {
+        const int c = i / NN, k = i - (i / NN) * NN;
+        const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
+        const int lc = (ry + 1) * BW + rx + 1;
+        const int a = k / N, b = k - (k / N) * N;
+        sFx[lc * NN + k] = op_x_at<T, N>(sPsi, tPxR, tPxL, C.dx, lc, a, b);
+        sGx[lc * NN + k] = op_x_at<T, N>(sOm, tOxR, tOxL, C.dx, lc, a, b);
+      } else {
+        const int ii = i - n1;
+        const int c = ii / NN, k = ii - (ii / NN) * NN;
+        const int w = B.TXe + 2;
+        const int ry = c / w, rx = c - (c / w) * w - 1;
+        const int lc = (ry + 1) * BW + rx + 1;
+        const int a = k / N, b = k - (k / N) * N;
+        sFy[lc * NN + k] = op_y_at<T, N>(sPsi, tPyR, tPyL, C.dy, lc, BW, a, b);
+        sGy[lc * NN + k] = op_y_at<T, N>(sOm, tOyR, tOyL, C.dy, lc, BW, a, b);
+      }
+    }
+  }
+  __syncthreads();
+
+  // S3a: J++ = f_x g_y - f_y g_x on the tile.
+  const int nin = B.TYe * B.TXe * NN;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+    sJ[o] = prod_diff(sFx[o], sGy[o], sFy[o], sGx[o]);
+  }
+  __syncthreads();
+
+  // S3b: h1 = f g_y - f_y g (in place of f_y), h2 = f_x g - f g_x (in place of f_x).
+  {
+    const int n1 = B.TYe * (B.TXe + 2) * NN;
+    const int n2 = (B.TYe + 2) * B.TXe * NN;
+    for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+      if (i < n1) {
+        const int c = i / NN, k = i - (i / NN) * NN;
+        const int w = B.TXe + 2;
+        const int ry = c / w, rx = c - (c / w) * w - 1;
+        const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+        sFy[o] = prod_diff(sPsi[o], sGy[o], sFy[o], sOm[o]);
+      } else {
+        const int ii = i - n1;
+        const int c = ii / NN, k = ii - (ii / NN) * NN;
+        const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
+        const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+        sFx[o] = prod_diff(sFx[o], sOm[o], sPsi[o], sGx[o]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // S4: traces of h1 along x and of h2 along y (reusing the psi trace arrays).
+  line_traces<T, N>(B, sFy, sFx, C.dx, C.dy, tPxR, tPxL, tPyR, tPyL, false);
+  __syncthreads();
+
+  // S5: J = (J++ + D_x h1 + D_y h2) / 3 = (J++ + J+x + Jx+) / 3, the viscous term and the update.
+  const T third = T(1.0 / 3.0);
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int lc = (ry + 1) * BW + rx + 1;
+    const int a = k / N, b = k - (k / N) * N;
+    const T dxh1 = op_x_at<T, N>(sFy, tPxR, tPxL, C.dx, lc, a, b);
+    const T dyh2 = op_y_at<T, N>(sFx, tPyR, tPyL, C.dy, lc, BW, a, b);
+    const T J = ((sJ[lc * NN + k] + dxh1) + dyh2) * third;
+    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+    if (A.bracket_only) {
+      A.omega_out[g] = double(J);
+      continue;
+    }
+    T R = -J;
+    if (A.visc != 0.0) {
+      const T lap = op_x_at<T, N>(sOm, tLxR, tLxL, C.lx, lc, a, b) + op_y_at<T, N>(sOm, tLyR, tLyL, C.ly, lc, BW, a, b);
+      R = fma(-T(A.visc), lap, R);  // + D Delta_h omega, since -Delta_h = lx + ly
+    }
+    double incr = A.c_new * double(R);
+    for (int m = 0; m < A.nhist; ++m) incr = fma(A.c_hist[m], double(A.hist[m][g]), incr);
+    if (A.R_out) A.R_out[g] = R;
+    A.omega_out[g] = fma(A.dt, incr, A.omega_base[g]);
+  }
+}
+
+// =========================================================================================
+// Operator application: mode 0  y = A x = W^1/2 (W^-1/2 A W^-1/2) W^1/2 x,
+//                       mode 1  y = Delta_h x = -(lx + ly) x.
+// =========================================================================================
+template <typename T, int N>
+__host__ __device__ constexpr size_t apply_smem_values(int TY, int TX) {
+  return (size_t)(TY + 2) * (TX + 2) * (N * N + 4 * N);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+                                                        const double* __restrict__ x, double* __restrict__ y,
+                                                        int mode) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  const int boxc = (G.TY + 2) * (G.TX + 2);
+  T *tXR = sU + boxc * NN, *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
+  const TileBox B = make_box(G, blockIdx.x);
+  const Op1D<T, N>& ox = mode == 0 ? C.kx : C.lx;
+  const Op1D<T, N>& oy = mode == 0 ? C.ky : C.ly;
+  stage_box<T, N>(G, B, sU, false, [&](size_t g, int k, bool) {
+    return mode == 0 ? T(x[g]) * C.sw[k] : T(x[g]);
+  });
+  __syncthreads();
+  line_traces<T, N>(B, sU, sU, ox, oy, tXR, tXL, tYR, tYL, false);
+  __syncthreads();
+  const int nin = B.TYe * B.TXe * NN;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int lc = (ry + 1) * B.BW + rx + 1;
+    const int a = k / N, b = k - (k / N) * N;
+    const T q = op_x_at<T, N>(sU, tXR, tXL, ox, lc, a, b) + op_y_at<T, N>(sU, tYR, tYL, oy, lc, B.BW, a, b);
+    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+    y[g] = mode == 0 ? double(q * C.sw[k]) : -double(q);
+  }
+}
+
+// =========================================================================================
+// Persistent conjugate-gradient solve of  Ahat y = b,  Ahat = W^-1/2 A W^-1/2  (plain CG on
+// the symmetrically scaled system = CG on A psi = W omega preconditioned by W^-1, Sec. 6).
+// Phases are separated by a capped grid barrier; dot products are block partials summed by
+// every block in a fixed order (bit-identical scalars in all blocks, so every block takes the
+// same branch).  Partial buffers alternate between two halves so that a block writing the
+// next partial never races a slower block still reading the previous ones.
+// =========================================================================================
+struct SolveStatus {
+  long long total_iters;
+  int last_iters;
+  int max_iters;
+  int flags;        // OR of all solves' flags
+  int last_flags;
+  int nsolves;
+  int last_sweeps;  // refinement sweeps of the last mixed solve
+  double last_rho;  // r.r of the last solve (scaled space)
+  double last_rhob; // b.b
+};
+
+template <typename T>
+struct CgVectors {
+  T* y;      // solution (scaled space)
+  T* r;      // residual
+  T* p0;     // search directions (double-buffered: a phase reads one, writes the other)
+  T* p1;
+  T* q;      // Ahat p
+};
+
+// One CG tile pass: stage u = load(...) (plus-shaped halo), apply Ahat, hand (g, k, u, q)
+// to out(...).
+template <typename T, int N, class LoadF, class OutF>
+__device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& G, int tile, T* sU, T* tXR,
+                                              T* tXL, T* tYR, T* tYL, LoadF&& load, OutF&& out) {
+  constexpr int NN = N * N;
+  const TileBox B = make_box(G, tile);
+  stage_box<T, N>(G, B, sU, false, load);
+  __syncthreads();
+  line_traces<T, N>(B, sU, sU, C.kx, C.ky, tXR, tXL, tYR, tYL, false);
+  __syncthreads();
+  const int nin = B.TYe * B.TXe * NN;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int lc = (ry + 1) * B.BW + rx + 1;
+    const int a = k / N, b = k - (k / N) * N;
+    const T q = op_x_at<T, N>(sU, tXR, tXL, C.kx, lc, a, b) + op_y_at<T, N>(sU, tYR, tYL, C.ky, lc, B.BW, a, b);
+    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+    out(g, k, sU[lc * NN + k], q);
+  }
+  __syncthreads();
+}
+
+// Right-hand side of the scaled system at node k of global offset g:
+//   b = rhs[g] if rhs is given, else sqrt(W_k) (omega[g] - wbar).
+template <typename T>
+struct RhsSource {
+  const double* omega;
+  const T* rhs;
+  T wbar;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ T rhs_at(const Ops2D<T, N>& C, const RhsSource<T>& B, size_t g, int k) {
+  return B.rhs ? B.rhs[g] : C.sw[k] * (T(B.omega[g]) - B.wbar);
+}
+
+// Restarts from the true residual allowed after the recursive one has met the tolerance.
+constexpr int kMaxRestarts = 20;
+
+// The CG iterations proper, from r (residual of the current y) with rho = r.r, rhob = b.b.
+// The stopping rule is on the true residual: when the recursive residual meets the
+// tolerance, one more tile pass computes b - Ahat y; if that misses the tolerance, CG
+// restarts from it (p = r).  Returns the iteration count; raises flags.
+// part: 4 * gridDim.x values of scratch.
+template <typename T, int N>
+__device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, const CgVectors<T>& V,
+                                          const RhsSource<T>& Bsrc, T* part, int& phase, SyncState* sync,
+                                          int* s_flag, T* sU, T* tXR, T* tXL, T* tYR, T* tYL, T* red, T* bcast,
+                                          T& rho, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
+                                          int max_restarts = kMaxRestarts) {
+  constexpr int NN = N * N;
+  const int ntiles = G.tilesX * G.tilesY;
+  const size_t ndof = (size_t)G.Nx * G.Ny * NN;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  int it = 0, restarts = 0;
+  T beta = T(0);
+  int cur = 0;
+  bool first = true;  // p = r (no previous direction)
+  while (true) {
+    if (fixed_iters > 0) {
+      if (it >= fixed_iters) break;
+    } else if (double(rho) <= tol2 * double(rhob)) {
+      if (max_restarts == 0) break;  // loose inner solves: the recursive residual suffices
+      // Verify on the true residual r = b - Ahat y.
+      T rt = T(0);
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        cg_tile_apply<T, N>(
+            C, G, t, sU, tXR, tXL, tYR, tYL, [&](size_t g, int, bool) { return __ldcg(V.y + g); },
+            [&](size_t g, int k, T, T qv) {
+              const T r = rhs_at<T, N>(C, Bsrc, g, k) - qv;
+              __stcg(V.r + g, r);
+              rt = fma(r, r, rt);
+            });
+      }
+      T* ph = part + (phase & 1) * 2 * gridDim.x;
+      ++phase;
+      rt = block_sum(rt, red);
+      if (threadIdx.x == 0) __stcg(ph + blockIdx.x, rt);
+      if (!grid_barrier(sync, s_flag)) {
+        flags |= kFlagTimeout;
+        return it;
+      }
+      const T rho_true = sum_partials(ph, gridDim.x, 1, bcast);
+      rho = rho_true;
+      if (double(rho_true) <= tol2 * double(rhob)) break;
+      if (restarts >= max_restarts) {
+        flags |= kFlagNoconv;
+        break;
+      }
+      ++restarts;
+      first = true;
+      continue;
+    }
+    if (rho == T(0)) break;
+    if (it >= maxit) {
+      flags |= kFlagNoconv;
+      break;
+    }
+    T* pin = cur ? V.p1 : V.p0;
+    T* pout = cur ? V.p0 : V.p1;
+    // Phase A: p = r + beta p_old (halo recomputed locally), q = Ahat p, p.q.
+    T pq = T(0);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      cg_tile_apply<T, N>(
+          C, G, t, sU, tXR, tXL, tYR, tYL,
+          [&](size_t g, int, bool interior) {
+            const T rv = __ldcg(V.r + g);
+            const T pv = first ? rv : fma(beta, __ldcg(pin + g), rv);
+            if (interior) __stcg(pout + g, pv);
+            return pv;
+          },
+          [&](size_t g, int, T pv, T qv) {
+            __stcg(V.q + g, qv);
+            pq = fma(pv, qv, pq);
+          });
+    }
+    T* ph = part + (phase & 1) * 2 * gridDim.x;
+    ++phase;
+    pq = block_sum(pq, red);
+    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, pq);
+    if (!grid_barrier(sync, s_flag)) {
+      flags |= kFlagTimeout;
+      return it;
+    }
+    const T pqs = sum_partials(ph, gridDim.x, 1, bcast);
+    if (!(pqs > T(0))) {
+      flags |= kFlagBreakdown;
+      break;
+    }
+    const T alpha = rho / pqs;
+    // Phase B: y += alpha p, r -= alpha q, r.r  (pointwise, grid-stride).
+    T rr = T(0);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) {
+      const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
+      const T yv = fma(alpha, pv, __ldcg(V.y + i));
+      const T rv = fma(-alpha, qv, __ldcg(V.r + i));
+      __stcg(V.y + i, yv);
+      __stcg(V.r + i, rv);
+      rr = fma(rv, rv, rr);
+    }
+    ph = part + (phase & 1) * 2 * gridDim.x;
+    ++phase;
+    rr = block_sum(rr, red);
+    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, rr);
+    if (!grid_barrier(sync, s_flag)) {
+      flags |= kFlagTimeout;
+      return it;
+    }
+    const T rnew = sum_partials(ph, gridDim.x, 1, bcast);
+    beta = rnew / rho;
+    rho = rnew;
+    cur ^= 1;
+    first = false;
+    ++it;
+  }
+  return it;
+}
+
+template <typename T>
+struct CgArgs {
+  const double* omega;  // b = sqrt(W) (omega - mean_W omega) ...
+  const T* rhs;         // ... or b = rhs (scaled space) when non-null
+  const double* xa;     // initial guess y0 = ca xa + cb xb (null terms dropped), times
+  const double* xb;     // sqrt(W) when x_unscaled
+  double ca, cb;
+  int x_unscaled;
+  CgVectors<T> v;
+  double* psi_out;      // if non-null: psi = y / sqrt(W) at the end
+  T* part;              // 4 * gridDim.x
+  SyncState* sync;
+  SolveStatus* status;
+  double tol2;
+  int maxit, fixed_iters;
+  double sumW;
+};
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t cg_smem_values(int TY, int TX) {
+  return (size_t)(TY + 2) * (TX + 2) * (N * N + 4 * N);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+                                                     const __grid_constant__ CgArgs<T> A) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  const int boxc = (G.TY + 2) * (G.TX + 2);
+  T *tXR = sU + boxc * NN, *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
+  __shared__ T red[32];
+  __shared__ T bcast;
+  __shared__ int s_flag;
+  const int ntiles = G.tilesX * G.tilesY;
+  const size_t ndof = (size_t)G.Nx * G.Ny * NN;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  int phase = 0, flags = 0, it = 0;
+  T rho = T(0), rhob = T(0);
+
+  // P0: W-mean of omega, in two passes (the second removes the rounding left by the first,
+  // so that b carries no rounding-sized component along the kernel of A).
+  T wbar = T(0);
+  if (A.rhs == nullptr) {
+    for (int pass = 0; pass < 2; ++pass) {
+      T s = T(0);
+      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+        s = fma(C.wq[i % NN], T(A.omega[i]) - wbar, s);
+      T* ph = A.part + (phase & 1) * 2 * gridDim.x;
+      ++phase;
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) __stcg(ph + blockIdx.x, s);
+      if (!grid_barrier(A.sync, &s_flag)) {
+        flags |= kFlagTimeout;
+        goto finish;
+      }
+      wbar += sum_partials(ph, gridDim.x, 1, &bcast) / T(A.sumW);
+    }
+  }
+  // P1: y0, b, r0 = b - Ahat y0, rho0 = r0.r0, rhob = b.b.
+  {
+    T rr = T(0), bb = T(0);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      cg_tile_apply<T, N>(
+          C, G, t, sU, tXR, tXL, tYR, tYL,
+          [&](size_t g, int k, bool interior) {
+            double v = 0.0;
+            if (A.xa) v = A.ca * A.xa[g];
+            if (A.xb) v = fma(A.cb, A.xb[g], v);
+            T tv = A.x_unscaled ? T(v) * C.sw[k] : T(v);
+            if (interior) __stcg(A.v.y + g, tv);
+            return tv;
+          },
+          [&](size_t g, int k, T, T qv) {
+            const T b = rhs_at<T, N>(C, RhsSource<T>{A.omega, A.rhs, wbar}, g, k);
+            const T r = b - qv;
+            __stcg(A.v.r + g, r);
+            rr = fma(r, r, rr);
+            bb = fma(b, b, bb);
+          });
+    }
+    T* ph = A.part + (phase & 1) * 2 * gridDim.x;
+    ++phase;
+    rr = block_sum(rr, red);
+    if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, rr);
+    bb = block_sum(bb, red);
+    if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, bb);
+    if (!grid_barrier(A.sync, &s_flag)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+    rho = sum_partials(ph, gridDim.x, 2, &bcast);
+    rhob = sum_partials(ph + 1, gridDim.x, 2, &bcast);
+  }
+  if (rhob == T(0)) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.v.y + i, T(0));
+    rho = T(0);
+  } else {
+    it = cg_iterate<T, N>(C, G, A.v, RhsSource<T>{A.omega, A.rhs, wbar}, A.part, phase, A.sync, &s_flag, sU,
+                          tXR, tXL, tYR, tYL, red, &bcast, rho, rhob, A.tol2, A.maxit, A.fixed_iters, flags);
+  }
+finish:
+  if (A.psi_out && !(flags & kFlagTimeout)) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+      A.psi_out[i] = double(__ldcg(A.v.y + i) * C.isw[i % NN]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveStatus* st = A.status;
+    st->total_iters += it;
+    st->last_iters = it;
+    st->max_iters = max(st->max_iters, it);
+    st->last_flags = flags;
+    st->flags |= flags;
+    st->nsolves += 1;
+    st->last_sweeps = 0;
+    st->last_rho = double(rho);
+    st->last_rhob = double(rhob);
+  }
+}
+
+// =========================================================================================
+// Mixed precision Poisson solve (iterative refinement, all on the device):
+//   y  <- y0;  r = b - Ahat y  in float64
+//   while r.r > tol^2 b.b:  solve Ahat e = r in float32 by CG from e = 0 to the relative
+//                           tolerance tol_in;  y += e (float64);  r = b - Ahat y (float64)
+// The float64 residual is the true residual of the float64 iterate, so the outer stopping
+// rule needs no further check.
+// =========================================================================================
+struct MixedArgs {
+  const double* omega;
+  const double* xa;
+  const double* xb;
+  double ca, cb;
+  int x_unscaled;
+  double* y;           // float64 solution (scaled space)
+  double* psi_out;     // if non-null: psi = y / sqrt(W) at the end
+  float* rf;           // float32 copy of the float64 residual (inner right-hand side)
+  CgVectors<float> v;  // inner solve: y = e, r, p0, p1, q
+  double* partd;       // 4 * gridDim.x
+  float* partf;        // 4 * gridDim.x
+  SyncState* sync;
+  SolveStatus* status;
+  double tol2, tol_in2;
+  int max_sweeps, maxit_in;
+  double sumW;
+};
+
+template <int N>
+__host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX) {
+  return cg_smem_values<double, N>(TY, TX) * sizeof(double);
+}
+
+// One float64 residual pass: r = b - Ahat y (y staged with halo), rf = float(r), inner
+// residual = rf, e = 0.  Returns this block's r.r and b.b.
+template <int N>
+__device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const Geom& G, const MixedArgs& A,
+                                               double wbar, bool from_x0, double* sU, double* tXR, double* tXL,
+                                               double* tYR, double* tYL, double& rr, double& bb) {
+  const int ntiles = G.tilesX * G.tilesY;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    cg_tile_apply<double, N>(
+        Cd, G, t, sU, tXR, tXL, tYR, tYL,
+        [&](size_t g, int k, bool interior) {
+          if (!from_x0) return __ldcg(A.y + g);
+          double v = 0.0;
+          if (A.xa) v = A.ca * A.xa[g];
+          if (A.xb) v = fma(A.cb, A.xb[g], v);
+          if (A.x_unscaled) v *= Cd.sw[k];
+          if (interior) __stcg(A.y + g, v);
+          return v;
+        },
+        [&](size_t g, int k, double, double qv) {
+          const double b = Cd.sw[k] * (A.omega[g] - wbar);
+          const double r = b - qv;
+          const float r32 = float(r);
+          __stcg(A.rf + g, r32);
+          __stcg(A.v.r + g, r32);
+          __stcg(A.v.y + g, 0.0f);
+          rr = fma(r, r, rr);
+          bb = fma(b, b, bb);
+        });
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
+                                                           const __grid_constant__ Ops2D<float, N> Cf, const Geom G,
+                                                           const __grid_constant__ MixedArgs A) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int boxc = (G.TY + 2) * (G.TX + 2);
+  double* sUd = reinterpret_cast<double*>(smem_raw);
+  double *tXRd = sUd + boxc * NN, *tXLd = tXRd + boxc * N, *tYRd = tXLd + boxc * N, *tYLd = tYRd + boxc * N;
+  float* sUf = reinterpret_cast<float*>(smem_raw);
+  float *tXRf = sUf + boxc * NN, *tXLf = tXRf + boxc * N, *tYRf = tXLf + boxc * N, *tYLf = tYRf + boxc * N;
+  __shared__ double redd[32];
+  __shared__ double bcd;
+  __shared__ float redf[32];
+  __shared__ float bcf;
+  __shared__ int s_flag;
+  const size_t ndof = (size_t)G.Nx * G.Ny * NN;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  int phase = 0, flags = 0, sweeps = 0;
+  long long inner = 0;
+  double rr = 0.0, bb = 0.0, wbar = 0.0;
+  for (int mp = 0; mp < 2; ++mp) {  // two-pass W-mean, as in cg_kernel
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+      s = fma(Cd.wq[i % NN], A.omega[i] - wbar, s);
+    double* ph = A.partd + (phase & 1) * 2 * gridDim.x;
+    ++phase;
+    s = block_sum(s, redd);
+    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, s);
+    if (!grid_barrier(A.sync, &s_flag)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+    wbar += sum_partials(ph, gridDim.x, 1, &bcd) / A.sumW;
+  }
+  for (int pass = 0;; ++pass) {
+    // float64 residual of the current iterate (pass 0: of the initial guess)
+    {
+      double r2 = 0.0, b2 = 0.0;
+      mixed_residual<N>(Cd, G, A, wbar, pass == 0, sUd, tXRd, tXLd, tYRd, tYLd, r2, b2);
+      double* ph = A.partd + (phase & 1) * 2 * gridDim.x;
+      ++phase;
+      r2 = block_sum(r2, redd);
+      if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, r2);
+      b2 = block_sum(b2, redd);
+      if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, b2);
+      if (!grid_barrier(A.sync, &s_flag)) {
+        flags |= kFlagTimeout;
+        goto finish;
+      }
+      rr = sum_partials(ph, gridDim.x, 2, &bcd);
+      bb = sum_partials(ph + 1, gridDim.x, 2, &bcd);
+    }
+    if (bb == 0.0) {
+      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.y + i, 0.0);
+      rr = 0.0;
+      break;
+    }
+    if (rr <= A.tol2 * bb) break;
+    if (sweeps >= A.max_sweeps) {
+      flags |= kFlagNoconv;
+      break;
+    }
+    // float32 inner CG from e = 0 on the residual equation
+    float rho_in = float(rr);
+    const float rhob_in = rho_in;
+    int fin = 0;
+    const int it_in = cg_iterate<float, N>(Cf, G, A.v, RhsSource<float>{nullptr, A.rf, 0.0f}, A.partf, phase, A.sync,
+                                           &s_flag, sUf, tXRf, tXLf, tYRf, tYLf, redf, &bcf, rho_in, rhob_in,
+                                           A.tol_in2, A.maxit_in, 0, fin, 0);
+    inner += it_in;
+    if (fin & kFlagTimeout) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+    // y += e
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+      __stcg(A.y + i, __ldcg(A.y + i) + double(__ldcg(A.v.y + i)));
+    if (!grid_barrier(A.sync, &s_flag)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+    ++sweeps;
+  }
+finish:
+  if (A.psi_out && !(flags & kFlagTimeout)) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+      A.psi_out[i] = __ldcg(A.y + i) * Cd.isw[i % NN];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveStatus* st = A.status;
+    const int it = int(inner);
+    st->total_iters += it;
+    st->last_iters = it;
+    st->max_iters = max(st->max_iters, it);
+    st->last_flags = flags;
+    st->flags |= flags;
+    st->nsolves += 1;
+    st->last_sweeps = sweeps;
+    st->last_rho = rr;
+    st->last_rhob = bb;
+  }
+}
+
+// =========================================================================================
+// Invariants: partial sums of W omega, W psi omega, W omega^2 per block, then one block
+// adds the partials in a fixed order.
+// =========================================================================================
+template <int N>
+struct NodeWeights {
+  double w[N * N];    // W_ab
+  double sw[N * N];   // sqrt(W_ab)
+  double isw[N * N];  // 1 / sqrt(W_ab)
+};
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) invariants_partial_kernel(const __grid_constant__ NodeWeights<N> W,
+                                                                     const double* __restrict__ psi,
+                                                                     const double* __restrict__ omega,
+                                                                     size_t ndof, int psi_scaled,
+                                                                     double* __restrict__ part) {
+  constexpr int NN = N * N;
+  __shared__ double red[32];
+  double v = 0.0, e = 0.0, o = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = int(i % NN);
+    const double w = omega[i];
+    const double p = psi_scaled ? psi[i] * W.isw[k] : psi[i];
+    const double ww = W.w[k] * w;
+    v += ww;
+    e = fma(ww, p, e);
+    o = fma(ww, w, o);
+  }
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x] = v;
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = e;
+  o = block_sum(o, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = o;
+}
+
+__global__ void invariants_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double bc;
+  for (int j = 0; j < 3; ++j) {
+    const double s = sum_partials(part + j, nparts, 3, &bc);
+    if (threadIdx.x == 0) out[j] = (j == 0) ? s : 0.5 * s;
+  }
+}
+
+// ---- small elementwise kernels ----------------------------------------------------------
+
+// y[i] = x[i] * s[i % NN]   (psi <-> sqrt(W) psi)
+template <int N>
+__global__ void scale_nodes_kernel(const __grid_constant__ NodeWeights<N> W, const double* __restrict__ x,
+                                   double* __restrict__ y, size_t ndof, int inverse) {
+  constexpr int NN = N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = int(i % NN);
+    y[i] = x[i] * (inverse ? W.isw[k] : W.sw[k]);
+  }
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ x, D* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = D(x[i]);
+}
+
+}  // namespace dgk

@@ -1,0 +1,28 @@
+// Host-side setup tables of the dG method (Sec. 4.1-4.2 and the LDG Laplacian of Sec. 6).
+//
+// All tables are dimensionless (reference cell [-1, 1]); the kernels scale them by the
+// cell sizes.  n = P = number of Gauss nodes / Legendre polynomials per dimension (1..5).
+#pragma once
+
+namespace dgk {
+
+constexpr int kMaxN = 5;
+
+struct RefTables {
+  int n;
+  double x[kMaxN], w[kMaxN];        // Gauss-Legendre abscissas and weights on [-1, 1]
+  // Central-flux derivative (Eq. discrete_der mapped to X-space, Eq. matrix_xspace):
+  //   h * (f_x)_c = C0 f_c + muR (lL . f_{c+1}) - muL (lR . f_{c-1})
+  double C0[kMaxN][kMaxN];          // B T^ 1/2 (D - D^T) F,   T^ = diag(2k+1)
+  double muR[kMaxN], muL[kMaxN];    // 1/2 B T^ p(+1), 1/2 B T^ p(-1)
+  double lL[kMaxN], lR[kMaxN];      // F^T p(-1), F^T p(+1): face values from nodal values
+  // LDG stiffness A1 = D+^T W D+ + tau sum_f j_f j_f^T (1D, per unit h; Sec. 6):
+  //   h * (A1 u)_c = A1cc u_c + betaA (lL . u_{c+1}) + lL (betaA . u_{c-1})
+  double A1cc[kMaxN][kMaxN];
+  double betaA[kMaxN];
+};
+
+// Fills t for 1 <= n <= kMaxN and penalty tau >= 0.  Returns 0 on success.
+int build_ref_tables(int n, double tau, RefTables* t);
+
+}  // namespace dgk

@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances (float64 path): relative L2 error <= 1e-12 per result, the bar for one step;
+bit-exact where the method fixes a result exactly (J(f, f) = 0, J(psi, 2 psi) = 0).
+Grids span several tiles and ragged tails (sizes not divisible by the tile), single-cell and
+non-square domains.
+"""
+import numpy as np
+import pytest
+
+from oracle.operators import Operators, dense_ops_2d, from_global, to_global
+from oracle.solver import pcg, poisson_rhs, solve_poisson, solve_poisson_dense
+from oracle.stepper import Simulation
+from oracle.tables import Grid as OGrid
+from paper_1311_7477_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel_l2(a, b, scale=0.0):
+    """||a - b|| / max(||b||, scale): scale is the size of the terms whose cancellation forms
+    b, for results that vanish in exact arithmetic (e.g. a bracket on a single cell row)."""
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), scale, 1e-300))
+
+
+# spectral radius of the central-flux derivative per unit h, n = 1..5 (|D| = rho / h)
+RHO_D = {1: 1.0, 2: 4.0, 3: 8.08, 4: 13.27, 5: 19.67}
+
+
+def bracket_scale(o, f, h):
+    """Rounding scale of J = (J++ + D_x h1 + D_y h2)/3: the parts' magnitudes plus the
+    products h1 = f h_y - f_y h, h2 = f_x h - f h_x before their derivative, times the
+    derivative's norm rho_D / h (an eps-sized rounding of a product of size P becomes an
+    error of eps P |D| after differentiation).  Where J is a small difference of large terms
+    (a shear layer with psi of size 1 and omega_y of size 400), or vanishes identically (one
+    periodic cell of n = 2, where D_y = 0), rounding is relative to this scale."""
+    g = o.g
+    parts = o.bracket_parts(f, h)
+    s_parts = np.abs(parts[0]) + np.abs(parts[1]) + np.abs(parts[2])
+    fx, fy, hx_, hy_ = o.Dx(f), o.Dy(f), o.Dx(h), o.Dy(h)
+    prods = (np.abs(f * hy_) + np.abs(fy * h)) / g.hx + (np.abs(fx * h) + np.abs(f * hx_)) / g.hy
+    return float(np.linalg.norm((s_parts + RHO_D[g.n] * prods).ravel()) / 3.0)
+
+
+GRIDS = [  # (Nx, Ny, n, Lx, Ly)
+    (13, 11, 1, 2 * np.pi, 2 * np.pi),
+    (19, 9, 2, 2.0, 3.0),
+    (21, 18, 3, 2 * np.pi, 2 * np.pi),
+    (17, 10, 4, 1.5, 1.0),
+    (11, 13, 5, 2 * np.pi, 2 * np.pi),
+    (1, 1, 3, 1.0, 1.0),
+    (1, 5, 4, 1.0, 2.0),
+    (6, 1, 2, 1.0, 1.0),
+]
+
+
+@pytest.fixture(scope="module")
+def dg(native):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return native
+
+
+@pytest.mark.parametrize("Nx,Ny,n,Lx,Ly", GRIDS)
+def test_bracket_parity(dg, Nx, Ny, n, Lx, Ly):
+    g = dg.Grid(Nx, Ny, n, Lx, Ly)
+    o = Operators(OGrid(Nx, Ny, n, Lx, Ly))
+    rng = np.random.default_rng(Nx * 100 + Ny + n)
+    f, h = rng.standard_normal((2, Ny, Nx, n, n))
+    J = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    dg.dg_bracket(g, dev(f), dev(h), J)
+    ref = o.bracket(f, h)
+    got = host(J)
+    S = bracket_scale(o, f, h)
+    err = rel_l2(got, ref, S)
+    assert err < 1e-12, err
+    # the integral constraints of Eqs. average1-3 hold for the GPU result too
+    scale = S / np.sqrt(got.size) * np.abs(f).max() * Lx * Ly
+    for w in (np.ones_like(f), f, h):
+        assert abs(o.inner(w, got)) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_bracket_bitwise_zeros(dg, n):
+    g = dg.Grid(10, 7, n, 2.0, 1.0)
+    og = OGrid(10, 7, n, 2.0, 1.0)
+    f = np.random.default_rng(1).standard_normal(g.shape)
+    J = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    dg.dg_bracket(g, dev(f), dev(f), J)
+    assert np.array_equal(host(J), np.zeros(g.shape))
+    X, Y = og.mesh()
+    psi = fields.sin_sin(X, Y)
+    dg.dg_bracket(g, dev(psi), dev(2.0 * psi), J)
+    assert np.array_equal(host(J), np.zeros(g.shape))
+    # antisymmetry to roundoff
+    h = np.random.default_rng(2).standard_normal(g.shape)
+    J2 = torch.empty_like(J)
+    dg.dg_bracket(g, dev(f), dev(h), J)
+    dg.dg_bracket(g, dev(h), dev(f), J2)
+    a, b = host(J), host(J2)
+    assert np.abs(a + b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("Nx,Ny,n,Lx,Ly", GRIDS)
+@pytest.mark.parametrize("tau", [0.0, 0.4])
+def test_laplace_parity(dg, Nx, Ny, n, Lx, Ly, tau):
+    g = dg.Grid(Nx, Ny, n, Lx, Ly, tau)
+    o = Operators(OGrid(Nx, Ny, n, Lx, Ly), tau=tau)
+    u = np.random.default_rng(7 + n).standard_normal(g.shape)
+    y = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    dg.dg_laplace_apply(g, dev(u), y, 0)
+    assert rel_l2(host(y), o.A(u)) < 1e-12
+    dg.dg_laplace_apply(g, dev(u), y, 1)
+    assert rel_l2(host(y), o.laplacian(u)) < 1e-12
+
+
+@pytest.mark.parametrize("Nx,Ny,n,Lx,Ly", GRIDS[:5])
+def test_poisson_fixed_iterations_parity(dg, Nx, Ny, n, Lx, Ly):
+    """Same Krylov steps on both sides: x_m of PCG(A, W^-1) == x_m of CG on W^-1/2 A W^-1/2."""
+    g = dg.Grid(Nx, Ny, n, Lx, Ly)
+    o = Operators(OGrid(Nx, Ny, n, Lx, Ly))
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(g.shape)
+    x0 = 0.1 * rng.standard_normal(g.shape)
+    m = 15
+    ref = solve_poisson(o, w, x0, 1e-30, 1000, fixed_iters=m)
+    psi = dev(x0)
+    rc, it, relres = dg.dg_poisson_solve(g, dev(w), psi, 1e-30, 1000, fixed_iters=m)
+    assert it == m == ref.iters
+    assert rel_l2(host(psi), ref.x) < 1e-12, rel_l2(host(psi), ref.x)
+    assert abs(relres - ref.relres) <= 1e-9 * ref.relres
+
+
+@pytest.mark.parametrize("n", [1, 2, 4])
+def test_poisson_converged_matches_dense(dg, n):
+    Nx, Ny = 5, 4
+    g = dg.Grid(Nx, Ny, n, 1.3, 1.1)
+    og = OGrid(Nx, Ny, n, 1.3, 1.1)
+    w = np.random.default_rng(n).standard_normal(g.shape)
+    ref = from_global(solve_poisson_dense(dense_ops_2d(og), to_global(w)), n)
+    psi = dev(np.zeros(g.shape))
+    rc, it, relres = dg.dg_poisson_solve(g, dev(w), psi, 1e-14, 10000)
+    assert relres <= 1e-14
+    assert rel_l2(host(psi), ref) < 1e-12
+
+
+def test_poisson_errors(dg):
+    g = dg.Grid(16, 16, 3)
+    w = dev(np.random.default_rng(0).standard_normal(g.shape))
+    psi = dev(np.zeros(g.shape))
+    rc, it, _ = dg.dg_poisson_solve(g, w, psi, 1e-12, 3, check=False)
+    assert rc == dg.DG_ERR_NOCONV and it == 3
+    with pytest.raises(dg.DGError):
+        dg.dg_poisson_solve(g, w, psi, 0.0, 10)
+    # a zero right-hand side has the zero solution, at once
+    psi.fill_(1.0)
+    rc, it, _ = dg.dg_poisson_solve(g, dev(np.zeros(g.shape)), psi, 1e-12, 100)
+    assert it == 0 and torch.count_nonzero(psi).item() == 0
+    # a constant one leaves a b of rounding size (the two-pass mean keeps it off the kernel
+    # of A); psi stays at rounding level
+    psi.fill_(1.0)
+    rc, it, _ = dg.dg_poisson_solve(g, dev(np.full(g.shape, 3.0)), psi, 1e-12, 1000, check=False)
+    assert rc in (dg.DG_OK, dg.DG_ERR_NOCONV)
+    assert torch.abs(psi).max().item() < 1e-12
+
+
+@pytest.mark.parametrize("Nx,Ny,n,Lx,Ly", GRIDS[:5])
+def test_invariants_parity(dg, Nx, Ny, n, Lx, Ly):
+    g = dg.Grid(Nx, Ny, n, Lx, Ly)
+    o = Operators(OGrid(Nx, Ny, n, Lx, Ly))
+    rng = np.random.default_rng(11)
+    p, w = rng.standard_normal((2,) + g.shape)
+    got = dg.dg_invariants(g, dev(p), dev(w))
+    ref = o.invariants(p, w)
+    for a, b in zip(got, ref):
+        assert abs(a - b) <= 1e-13 * (1 + abs(b))
+    w[0, 0, 0, 0] = np.nan
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_invariants(g, dev(p), dev(w))
+    assert e.value.code == dg.DG_ERR_NONFINITE
+
+
+def _oracle_state(Nx, Ny, n, D, dt, steps, seed, fixed):
+    og = OGrid(Nx, Ny, n)
+    o = Operators(og)
+    X, Y = og.mesh()
+    w0 = fields.random_phase(X, Y, seed=seed, kmax=5)
+    sim = Simulation(o, w0, D, dt, tol=1e-13, K=3, fixed_iters=fixed)
+    sim.step(steps)
+    return o, sim
+
+
+@pytest.mark.parametrize("k", [0, 1, 3])
+@pytest.mark.parametrize("D", [0.0, 2e-3])
+def test_one_step_parity(dg, k, D):
+    """From the identical state (omega^k, psi^k, psi^{k-1}, R^{k-1}, R^{k-2}, k) both sides take
+    one step (RK4 for k < 2, AB3 after) with the same fixed CG iteration count."""
+    Nx, Ny, n, dt, m = 12, 10, 3, 2e-3, 40
+    o, osim = _oracle_state(Nx, Ny, n, D, dt, k, seed=5, fixed=m)
+    g = dg.Grid(Nx, Ny, n)
+    z = np.zeros(g.shape)
+    R1 = osim.R_hist[0] if len(osim.R_hist) > 0 else z
+    R2 = osim.R_hist[1] if len(osim.R_hist) > 1 else z
+    sim = dg.Sim(g, dev(osim.omega), D=D, dt=dt, cg_tol=1e-13)
+    sim.set_state(k, dev(osim.omega), dev(osim.psi), dev(osim.psi_prev), dev(R1), dev(R2))
+    sim.set_cg(1e-30, 1000, fixed_iters=m)
+    sim.step(1)
+    osim.step(1)
+    om, ps = torch.empty(g.shape, dtype=torch.float64, device="cuda"), torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    sim.get(om, ps)
+    assert rel_l2(host(om), osim.omega) < 1e-12, rel_l2(host(om), osim.omega)
+    assert rel_l2(host(ps), osim.psi) < 1e-12, rel_l2(host(ps), osim.psi)
+
+
+def test_trajectory_small_config(dg):
+    """32 x 32 cells, n = 3, omega0 = 2 sin x sin y + U(-1e-3, 1e-3) (seed 0), D = 0,
+    CG tol 1e-12, dt = 1e-3, 100 steps: both sides step independently."""
+    Nx = Ny = 32
+    n = 3
+    og = OGrid(Nx, Ny, n)
+    o = Operators(og)
+    X, Y = og.mesh()
+    w0 = fields.sin_sin_noise(X, Y, amp=1e-3, seed=0)
+    osim = Simulation(o, w0, 0.0, 1e-3, tol=1e-12, K=3)
+    g = dg.Grid(Nx, Ny, n)
+    sim = dg.Sim(g, dev(w0), D=0.0, dt=1e-3, cg_tol=1e-12)
+    inv0 = sim.invariants()
+    V0 = inv0[0]
+    for s in range(100):
+        sim.step(1)
+        if s % 10 == 9:
+            V = sim.invariants()[0]
+            assert abs(V - V0) < 1e-13 * 4 * np.pi ** 2 * np.abs(w0).max()
+    osim.step(100)
+    om, ps = torch.empty(g.shape, dtype=torch.float64, device="cuda"), torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    sim.get(om, ps)
+    assert rel_l2(host(om), osim.omega) < 1e-10
+    assert rel_l2(host(ps), osim.psi) < 1e-10
+    inv = sim.invariants()
+    oinv = osim.invariants()
+    for a, b in zip(inv[1:], oinv[1:]):
+        assert abs(a - b) < 1e-11 * abs(b)
+    info = sim.status()
+    assert info.step == 100 and info.status == 0
+
+
+def test_full_size_shear_layer_sampled(dg):
+    """512 x 512 cells, n = 4 (4.19M dof), double shear layer, D = 1e-4, dt = 5e-4, CG tol
+    1e-10 -- the launch configuration of the benchmark.  The oracle checks the bracket
+    everywhere, the Poisson solve through its residual and one update of omega."""
+    N, n, D, dt = 512, 4, 1e-4, 5e-4
+    g = dg.Grid(N, N, n)
+    og = OGrid(N, N, n)
+    o = Operators(og)
+    xn, yn, _ = g.nodes()
+    X, Y = fields.mesh_from_nodes(xn, yn)
+    w0 = fields.shear_layer(X, Y)
+    sim = dg.Sim(g, dev(w0), D=D, dt=dt, cg_tol=1e-10)
+    sim.step(3)
+    st = sim.status()
+    assert st.status == 0 and st.cg_relres_last <= 1e-10
+    shape = g.shape
+    bufs = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+    k = sim.get_state(*bufs)
+    om, ps, pp, R1, R2 = [host(b) for b in bufs]
+    # Poisson: the GPU psi solves A psi = W (omega - mean) to the stated tolerance.  The
+    # oracle re-evaluates the residual with its own rounding, which at this condition number
+    # (about 6e6) is itself uncertain by about eps * kappa ~ 1e-10: bound 2 tol.
+    b = poisson_rhs(o, om)
+    r = b - o.A(ps)
+    relres = np.sqrt(np.sum(r * r / o.W2) / np.sum(b * b / o.W2))
+    assert relres < 2e-10, relres
+    # bracket over the whole field
+    J = torch.empty(shape, dtype=torch.float64, device="cuda")
+    dg.dg_bracket(g, bufs[1], bufs[0], J)
+    assert rel_l2(host(J), o.bracket(ps, om), bracket_scale(o, ps, om)) < 1e-12
+    # one AB3 update of omega from this state
+    sim.step(1)
+    om1 = torch.empty(shape, dtype=torch.float64, device="cuda")
+    sim.get(om1, None)
+    Rk = -o.bracket(ps, om) + D * o.laplacian(om)
+    ref = om + dt * (23.0 * Rk - 16.0 * R1 + 5.0 * R2) / 12.0
+    assert rel_l2(host(om1), ref) < 1e-12
