@@ -127,6 +127,27 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
                      int fixed_iters, int* iters, double* relres, void* stream);
 
 /*
+ * dg_poisson_solve_static -- the Poisson solve of dg_poisson_solve for callers that must not
+ * allocate device memory: code that runs where cudaMalloc is not allowed or not safe (for
+ * example while another framework owns the device allocator, or around a stream capture
+ * that must not change the memory pool), and callers that cannot hold a dg_grid handle,
+ * since creating one allocates.  The paper has no counterpart; this is an interface choice.
+ * It takes the grid as plain parameters (Nx, Ny, n, Lx, Ly, tau as in dg_grid_create) and
+ * keeps all its scratch (CG vectors, partial sums, barrier and status words) in one
+ * file-scope device array of about 2.6 MB that every GPU loading the library holds until
+ * the process exits.  Grids are limited to Nx*Ny*n*n <= 65536 values; larger ones are
+ * rejected with DG_ERR_ARG.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the one array, which keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other host threads) race.  Arguments, results and errors otherwise as in
+ * dg_poisson_solve; synchronises the stream.
+ */
+int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double Ly, double tau, const double* omega,
+                            double* psi, double tol, int maxit, int fixed_iters, int* iters, double* relres,
+                            void* stream);
+
+/*
  * dg_invariants -- out[0..2] = (V, E, Omega) = (int omega, 1/2 int psi omega,
  * 1/2 int omega^2) by Gauss-Legendre quadrature (Eq. quantities, Eq. def_norm), summed in
  * float64 in a fixed order.  Synchronises the stream.  Errors: DG_ERR_NONFINITE if a sum is

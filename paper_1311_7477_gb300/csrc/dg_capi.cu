@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <mutex>
 #include <vector>
 
 #include "../../include/dg.h"
@@ -1003,3 +1004,126 @@ int dg_sim_invariants(dg_sim* s, double out[3], void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Poisson solve without any allocation (dg_poisson_solve_static)
+//
+// For callers that cannot allocate device memory themselves -- code running where
+// cudaMalloc is forbidden or unsafe, such as inside a CUDA stream capture that must not
+// change the memory pool, or in a host process whose allocator is owned by another
+// framework -- this entry point runs the same persistent CG kernel as dg_poisson_solve but
+// keeps every scratch vector, the per-block partial sums, the grid barrier and the status
+// word in one file-scope __device__ array of fixed size.  Each GPU that loads the library
+// holds that array (about 2.6 MB) until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr long long kStaticMaxDof = 65536;  // Nx * Ny * n * n accepted by the static solve
+constexpr int kStaticMaxBlocks = 4096;      // cooperative blocks the partials can hold
+
+struct StaticScratch {
+  double y[kStaticMaxDof];
+  double r[kStaticMaxDof];
+  double p0[kStaticMaxDof];
+  double p1[kStaticMaxDof];
+  double q[kStaticMaxDof];
+  double part[4 * kStaticMaxBlocks];
+  SyncState sync;
+  SolveStatus status;
+};
+
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+// The array's name in host code is a host-side stand-in, not a device address: the device
+// address is looked up once per device (with that device current) and cached.
+constexpr int kStaticMaxDevices = 64;
+StaticScratch* g_static_addr[kStaticMaxDevices] = {};
+std::mutex g_static_mu;
+
+int static_scratch_address(StaticScratch** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(DG_ERR_CUDA, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = static_cast<StaticScratch*>(p);
+  }
+  *out = g_static_addr[dev];
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double Ly, double tau, const double* omega,
+                                       double* psi, double tol, int maxit, int fixed_iters, int* iters,
+                                       double* relres, void* stream) {
+  if (n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
+  if (Nx < 1 || Ny < 1) return fail(DG_ERR_ARG, "Nx, Ny must be >= 1");
+  if (!(Lx > 0.0) || !(Ly > 0.0) || !(tau >= 0.0)) return fail(DG_ERR_ARG, "need Lx, Ly > 0 and tau >= 0");
+  const long long ndof = (long long)Nx * Ny * n * n;
+  if (ndof > kStaticMaxDof)
+    return fail(DG_ERR_ARG, "grid of %lld values exceeds the static scratch limit of %lld values (Nx*Ny*n*n)", ndof,
+                kStaticMaxDof);
+  if (!omega || !psi) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(omega) || !aligned8(psi)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (maxit < 0 || fixed_iters < 0) return fail(DG_ERR_ARG, "maxit and fixed_iters must be >= 0");
+  if (fixed_iters == 0 && !(tol > 0.0)) return fail(DG_ERR_ARG, "tol must be > 0");
+  cudaStream_t st = as_stream(stream);
+  StaticScratch* sc = nullptr;
+  if (int rc = static_scratch_address(&sc)) return rc;
+
+  // A grid description on the host stack, its workspace pointing into the static array.
+  dg_grid g{};
+  g.Nx = Nx;
+  g.Ny = Ny;
+  g.n = n;
+  g.Lx = Lx;
+  g.Ly = Ly;
+  g.hx = Lx / Nx;
+  g.hy = Ly / Ny;
+  g.tau = tau;
+  build_ref_tables(n, tau, &g.rt);
+  default_tiles(n, g.rTY, g.rTX, g.cTY, g.cTX);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  dispatch_n(n, [&](auto nc) {
+    build_ops<decltype(nc)::value>(&g);
+    return DG_OK;
+  });
+  Workspace w{};
+  w.ndof = (size_t)ndof;
+  w.grid_cap = kStaticMaxBlocks;
+  w.y = sc->y;
+  w.r = sc->r;
+  w.p0 = sc->p0;
+  w.p1 = sc->p1;
+  w.q = sc->q;
+  w.part = sc->part;
+  w.sync = &sc->sync;
+  w.status = &sc->status;
+  // The status word accumulates across calls: start it at zero (the barrier state is
+  // cleared by the launch itself).
+  CUDA_TRY(cudaMemsetAsync(&sc->status, 0, sizeof(SolveStatus), st));
+
+  CgArgs<double> A{};
+  A.omega = omega;
+  A.xa = psi;
+  A.ca = 1.0;
+  A.x_unscaled = 1;
+  A.v = CgVectors<double>{w.y, w.r, w.p0, w.p1, w.q};
+  A.psi_out = psi;
+  A.tol2 = tol * tol;
+  A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
+  A.fixed_iters = fixed_iters;
+  A.sumW = Lx * Ly;
+  int rc = dispatch_n(n, [&](auto nc) { return launch_cg<double, decltype(nc)::value>(&g, A, w, st); });
+  if (rc) return rc;
+  SolveStatus s;
+  if ((rc = read_status(w, &s, st))) return rc;
+  if (iters) *iters = s.last_iters;
+  if (relres) *relres = s.last_rhob > 0 ? std::sqrt(std::max(s.last_rho, 0.0) / s.last_rhob) : 0.0;
+  return flags_to_status(s.last_flags);
+}

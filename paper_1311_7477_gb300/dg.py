@@ -58,6 +58,7 @@ def _load():
         "dg_laplace_apply": (I, [P, P, P, I, P]),
         "dg_poisson_solve": (I, [P, P, P, D, I, I, PI, PD, P]),
         "dg_invariants": (I, [P, P, P, PD, P]),
+        "dg_poisson_solve_static": (I, [I, I, I, D, D, D, P, P, D, I, I, PI, PD, P]),
         "dg_sim_create": (I, [PP, P, D, D, I, D, I, P, P]),
         "dg_sim_destroy": (I, [P]),
         "dg_step": (I, [P, I, P]),
@@ -201,6 +202,19 @@ def dg_poisson_solve(grid, omega, psi, tol=1e-12, maxit=100000, fixed_iters=0, s
     rr = ctypes.c_double(0.0)
     rc = _lib.dg_poisson_solve(grid.h, _ptr(omega), _ptr(psi), float(tol), int(maxit), int(fixed_iters),
                                ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(rc)
+    return rc, it.value, rr.value
+
+
+def dg_poisson_solve_static(Nx, Ny, n, Lx, Ly, tau, omega, psi, tol=1e-12, maxit=100000, fixed_iters=0,
+                            stream=None, check=True):
+    """The allocation-free Poisson solve (no grid handle); returns (rc, iterations, relres)."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    rc = _lib.dg_poisson_solve_static(int(Nx), int(Ny), int(n), float(Lx), float(Ly), float(tau), _ptr(omega),
+                                      _ptr(psi), float(tol), int(maxit), int(fixed_iters), ctypes.byref(it),
+                                      ctypes.byref(rr), _stream(stream))
     if check:
         _check(rc)
     return rc, it.value, rr.value
