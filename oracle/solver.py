@@ -17,8 +17,15 @@ states only that a conjugate gradient method solves it; the details below are a 
 
 With x0 of W-mean zero all iterates stay W-mean zero, since every update direction
 z = W^{-1} r satisfies sum W z = sum r = 0.
+
+A second preconditioner (a choice of this build; Sec. 6 names none) is the additive
+two-level one of TwoLevel below: exact solves on every cell plus an exact solve of the
+Galerkin coarse problem on cell averages.  It leaves the solution unchanged and makes the
+iteration count independent of the mesh size.
 """
 import numpy as np
+
+from .operators import ldg_matrix_1d
 
 
 def poisson_rhs(ops, omega):
@@ -35,26 +42,73 @@ def poisson_rhs(ops, omega):
 MAX_RESTARTS = 20
 
 
+class TwoLevel:
+    """Additive two-level preconditioner  M^{-1} = B + P A_c^+ P^T  for A (Sec. 6 operator):
+
+    * B: on every cell, the inverse of the cell's own diagonal block of A,
+      A_cc = W_y (x) A1_cc,x + A1_cc,y (x) W_x  (A1_cc = the own-cell block of the 1D LDG
+      stiffness); identical for all cells of the uniform grid;
+    * P: prolongation of one value per cell to all nodes of the cell (piecewise constants);
+    * A_c = P^T A P: the Galerkin coarse operator on the cells -- periodic and translation
+      invariant, hence diagonalised by the 2D DFT; its eigenvalues are the DFT of its stencil
+      (A applied to the indicator of one cell, summed per cell).  A_c^+ is the pseudo-inverse
+      that drops the constant mode (A_c's kernel, the constants).
+    B and A_c^+ are symmetric and B is positive definite, so M^{-1} is symmetric positive
+    definite and PCG applies."""
+
+    def __init__(self, ops):
+        g = ops.g
+        n = g.n
+        t = g.t
+        A1x = ldg_matrix_1d(t, 3, g.hx, ops.tau)[n:2 * n, n:2 * n]
+        A1y = ldg_matrix_1d(t, 3, g.hy, ops.tau)[n:2 * n, n:2 * n]
+        Acc = np.kron(np.diag(ops.wy), A1x) + np.kron(A1y, np.diag(ops.wx))   # node index a*n + b
+        self.Binv = np.linalg.inv(Acc)
+        e = g.zeros()
+        e[0, 0] = 1.0
+        stencil = ops.A(e).sum(axis=(2, 3))                 # first column of A_c (circulant)
+        lam = np.fft.fft2(stencil).real
+        inv = np.zeros_like(lam)
+        nz = np.ones_like(lam, dtype=bool)
+        nz[0, 0] = False                                     # the constant mode
+        inv[nz] = 1.0 / lam[nz]
+        self.lam, self.lam_inv = lam, inv
+        self.n = n
+
+    def coarse_solve(self, rc):
+        """A_c^+ rc by the 2D DFT (rc of shape (Ny, Nx))."""
+        return np.fft.ifft2(np.fft.fft2(rc) * self.lam_inv).real
+
+    def __call__(self, r):
+        Ny, Nx, n, _ = r.shape
+        zb = np.einsum("ij,yxj->yxi", self.Binv, r.reshape(Ny, Nx, n * n)).reshape(r.shape)
+        uc = self.coarse_solve(r.sum(axis=(2, 3)))
+        return zb + uc[:, :, None, None]
+
+
 class CGResult:
     def __init__(self, x, iters, relres, converged):
         self.x, self.iters, self.relres, self.converged = x, iters, relres, converged
 
 
-def pcg(ops, b, x0, tol, maxit, fixed_iters=0):
-    """Preconditioned CG for A x = b with preconditioner W^{-1}.
+def pcg(ops, b, x0, tol, maxit, fixed_iters=0, precond=None):
+    """Preconditioned CG for A x = b; preconditioner W^{-1} (precond=None) or a callable
+    z = M^{-1} r (e.g. TwoLevel(ops)).
 
-    Stops when r.W^{-1}r <= tol^2 b.W^{-1}b (fixed_iters == 0) or after exactly
-    fixed_iters iterations (fixed_iters > 0); an exactly zero residual also stops.
+    Stops when r.W^{-1}r <= tol^2 b.W^{-1}b on the true residual (fixed_iters == 0) or after
+    exactly fixed_iters iterations (fixed_iters > 0); an exactly zero residual also stops.
     Returns a CGResult; converged is False when maxit was reached first."""
     W = ops.W2
+    M = precond if precond is not None else (lambda r: r / W)
     x = np.array(x0, dtype=np.float64, copy=True)
     rho_b = float(np.sum(b * b / W))
     if rho_b == 0.0:
         return CGResult(np.zeros_like(x), 0, 0.0, True)
     r = b - ops.A(x)
-    z = r / W
+    z = M(r)
     p = z.copy()
-    rho = float(np.sum(r * z))
+    rz = float(np.sum(r * z))
+    rr = float(np.sum(r * r / W))
     it = 0
     restarts = 0
     converged = True
@@ -62,40 +116,46 @@ def pcg(ops, b, x0, tol, maxit, fixed_iters=0):
         if fixed_iters > 0:
             if it == fixed_iters:
                 break
-        elif rho <= tol * tol * rho_b:
+        elif rr <= tol * tol * rho_b:
             r_true = b - ops.A(x)
-            rho_true = float(np.sum(r_true * r_true / W))
-            if rho_true <= tol * tol * rho_b or restarts == MAX_RESTARTS:
-                rho = rho_true
-                converged = rho_true <= tol * tol * rho_b
+            rr_true = float(np.sum(r_true * r_true / W))
+            if rr_true <= tol * tol * rho_b or restarts == MAX_RESTARTS:
+                rr = rr_true
+                converged = rr_true <= tol * tol * rho_b
                 break
             restarts += 1
             r = r_true
-            z = r / W
+            z = M(r)
             p = z.copy()
-            rho = float(np.sum(r * z))
+            rz = float(np.sum(r * z))
+            rr = rr_true
             continue
-        if rho == 0.0:
+        if rr == 0.0:
             break
         if it == maxit:
             converged = False
             break
         q = ops.A(p)
-        alpha = rho / float(np.sum(p * q))
+        alpha = rz / float(np.sum(p * q))
         x = x + alpha * p
         r = r - alpha * q
-        z = r / W
-        rho_new = float(np.sum(r * z))
-        beta = rho_new / rho
+        z = M(r)
+        rz_new = float(np.sum(r * z))
+        rr = float(np.sum(r * r / W))
+        beta = rz_new / rz
         p = z + beta * p
-        rho = rho_new
+        rz = rz_new
         it += 1
-    return CGResult(x, it, float(np.sqrt(max(rho, 0.0) / rho_b)), converged)
+    if precond is not None:
+        # A preconditioner other than W^{-1} may move x along the constants (the kernel of
+        # A, invisible to the residual); the solution is the W-mean-zero one (G7 reading).
+        x = x - float(np.sum(W * x)) / float(np.sum(W))
+    return CGResult(x, it, float(np.sqrt(max(rr, 0.0) / rho_b)), converged)
 
 
-def solve_poisson(ops, omega, x0, tol, maxit, fixed_iters=0):
+def solve_poisson(ops, omega, x0, tol, maxit, fixed_iters=0, precond=None):
     """psi with -Delta_h psi = omega - mean_W(omega), by pcg from x0."""
-    return pcg(ops, poisson_rhs(ops, omega), x0, tol, maxit, fixed_iters)
+    return pcg(ops, poisson_rhs(ops, omega), x0, tol, maxit, fixed_iters, precond)
 
 
 def solve_poisson_dense(dense, omega_global):

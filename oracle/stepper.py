@@ -28,8 +28,11 @@ class Simulation:
     """State: omega^k, psi^k, psi^{k-1}, the history R^{k-1}, R^{k-2}, ... and k."""
 
     def __init__(self, ops, omega0, D, dt, tol=1e-12, maxit=100000, K=3,
-                 fixed_iters=0, psi0=None):
+                 fixed_iters=0, psi0=None, precond="jacobi"):
+        """precond: "jacobi" (W^{-1}) or "twolevel" (solver.TwoLevel)."""
         self.ops, self.D, self.dt = ops, float(D), float(dt)
+        from .solver import TwoLevel
+        self.precond = TwoLevel(ops) if precond == "twolevel" else None
         self.tol, self.maxit, self.K, self.fixed_iters = float(tol), int(maxit), int(K), int(fixed_iters)
         self.omega = np.array(omega0, dtype=np.float64, copy=True)
         if psi0 is None:
@@ -42,7 +45,7 @@ class Simulation:
         self.cg_iters = []
 
     def solve(self, omega, x0):
-        res = solve_poisson(self.ops, omega, x0, self.tol, self.maxit, self.fixed_iters)
+        res = solve_poisson(self.ops, omega, x0, self.tol, self.maxit, self.fixed_iters, self.precond)
         if not res.converged:
             raise RuntimeError("CG did not converge within maxit")
         self.cg_iters_last = res.iters
