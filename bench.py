@@ -239,6 +239,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "twolevel"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -269,6 +270,7 @@ def main():
     precision = dg.DG_FP64 if args.precision == "fp64" else dg.DG_MIXED
     N, n = wl["N"], wl["n"]
     g = dg.Grid(N, N, n)
+    g.set_precond(args.precond)
     dof = g.dof
     xn, yn, _ = g.nodes()
     X, Y = fields.mesh_from_nodes(xn, yn)
@@ -390,7 +392,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-            "config": dict(_config(args.workload, wl, args.precision),
+            "config": dict(_config(args.workload, wl, args.precision), cg_preconditioner=args.precond,
                            l2=("no flush: the per-step working set (%.0f MB of state and CG vectors) exceeds "
                                "the 129 MB L2" % (12 * dof * 8 / 1e6))),
             "cg_iters_per_step": iters, "rhs_ms": rhs_ms_per_launch, "roofline": roof,

@@ -42,6 +42,10 @@ extern "C" {
 #define DG_ERR_NONFINITE 5  /* a reduction saw a NaN or Inf                                */
 #define DG_ERR_TIMEOUT 6    /* a device-side wait hit its iteration cap                    */
 
+/* ---- CG preconditioners (Sec. 6 names none; see dg_grid_set_precond) ---------------- */
+#define DG_PRECOND_JACOBI 0    /* W^-1: the inverse diagonal mass matrix (default)          */
+#define DG_PRECOND_TWOLEVEL 1  /* cell block solves + DFT coarse solve on cell averages    */
+
 /* ---- precision modes ------------------------------------------------------------- */
 #define DG_FP64 0   /* everything in float64                                               */
 #define DG_MIXED 1  /* bracket and inner CG in float32, float64 refinement, state and sums */
@@ -95,6 +99,18 @@ int dg_grid_nodes(const dg_grid* g, double* x_nodes, double* y_nodes, double* we
  * 0 restores the built-in choice for this n.  Used by the autotuner.  Errors: DG_ERR_ARG.
  */
 int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
+
+/*
+ * dg_grid_set_precond -- the CG preconditioner of every later Poisson solve on this grid
+ * (dg_poisson_solve and the simulations on g).  Sec. 6 only says that the symmetric dG
+ * Poisson system is solved by conjugate gradients; the choice does not change what CG
+ * converges to.  DG_PRECOND_JACOBI: W^-1.  DG_PRECOND_TWOLEVEL: the additive two-level
+ * preconditioner B + P A_c^+ P^T -- B the exact inverse of every cell's diagonal block of
+ * A, P the prolongation of cell values to the cell's nodes, A_c = P^T A P the Galerkin
+ * coarse operator, inverted (constant mode dropped) by a 2D DFT of the cell grid; the
+ * solution is returned with zero W-mean.  Errors: DG_ERR_ARG.
+ */
+int dg_grid_set_precond(dg_grid* g, int kind);
 
 /*
  * dg_bracket -- J = {psi, omega} by the conservative dG Arakawa bracket

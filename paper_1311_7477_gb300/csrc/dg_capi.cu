@@ -152,6 +152,11 @@ struct Workspace {
   // float32 inner-solve vectors of the mixed precision path
   float *rf = nullptr, *fr = nullptr, *fe = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fq = nullptr;
   float* partf = nullptr;
+  // two-level preconditioner work arrays (float64 and, for the mixed path, float32)
+  double *pz = nullptr, *prc = nullptr, *puc = nullptr;
+  Cplx<double>* pC = nullptr;
+  float *pzf = nullptr, *prcf = nullptr, *pucf = nullptr;
+  Cplx<float>* pCf = nullptr;
   SyncState* sync = nullptr;
   SolveStatus* status = nullptr;
   double* inv_part = nullptr;  // 3 * kInvBlocks
@@ -161,6 +166,17 @@ struct Workspace {
 
 constexpr int kInvBlocks = 1024;
 
+// Device tables of the two-level preconditioner (see PrecondArgs), float64 and float32.
+struct PcTables {
+  double* Bt = nullptr;
+  Cplx<double>*twx = nullptr, *twy = nullptr;
+  double *ax = nullptr, *ay = nullptr;
+  float* Btf = nullptr;
+  Cplx<float>*twxf = nullptr, *twyf = nullptr;
+  float *axf = nullptr, *ayf = nullptr;
+  int log2x = -1, log2y = -1;
+};
+
 struct dg_grid {
   int Nx, Ny, n;
   double Lx, Ly, hx, hy, tau;
@@ -169,6 +185,8 @@ struct dg_grid {
   int num_sms;
   OpsHost ops;
   Workspace ws;
+  int precond = 0;  // DG_PRECOND_JACOBI or DG_PRECOND_TWOLEVEL
+  PcTables pc;
 };
 
 struct dg_sim {
@@ -214,6 +232,14 @@ void free_ws(Workspace& w) {
   cudaFree(w.fp1);
   cudaFree(w.fq);
   cudaFree(w.partf);
+  cudaFree(w.pz);
+  cudaFree(w.prc);
+  cudaFree(w.puc);
+  cudaFree(w.pC);
+  cudaFree(w.pzf);
+  cudaFree(w.prcf);
+  cudaFree(w.pucf);
+  cudaFree(w.pCf);
   if (w.host_out) cudaFreeHost(w.host_out);
   w = Workspace{};
 }
@@ -235,6 +261,20 @@ int alloc_ws(Workspace& w, size_t ndof, int grid_cap, bool with_y) {
   CUDA_TRY(cudaMalloc(&w.inv_part, 3 * (size_t)kInvBlocks * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w.inv_out, 3 * sizeof(double)));
   CUDA_TRY(cudaMallocHost(&w.host_out, 3 * sizeof(double)));
+  return DG_OK;
+}
+
+int alloc_ws_precond(Workspace& w, size_t ncell, bool mixed) {
+  CUDA_TRY(cudaMalloc(&w.pz, w.ndof * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.prc, ncell * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.puc, ncell * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.pC, ncell * sizeof(Cplx<double>)));
+  if (mixed) {
+    CUDA_TRY(cudaMalloc(&w.pzf, w.ndof * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&w.prcf, ncell * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&w.pucf, ncell * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&w.pCf, ncell * sizeof(Cplx<float>)));
+  }
   return DG_OK;
 }
 
@@ -293,6 +333,166 @@ int set_smem(Kern k, size_t bytes) {
   return DG_OK;
 }
 
+// ---- two-level preconditioner tables ---------------------------------------------------
+
+void free_pc(PcTables& t) {
+  cudaFree(t.Bt);
+  cudaFree(t.twx);
+  cudaFree(t.twy);
+  cudaFree(t.ax);
+  cudaFree(t.ay);
+  cudaFree(t.Btf);
+  cudaFree(t.twxf);
+  cudaFree(t.twyf);
+  cudaFree(t.axf);
+  cudaFree(t.ayf);
+  t = PcTables{};
+}
+
+int log2_exact(int L) {
+  int k = 0;
+  while ((1 << k) < L) ++k;
+  return (1 << k) == L ? k : -1;
+}
+
+// Gauss-Jordan inverse with partial pivoting of an m x m matrix (row-major, in place into inv).
+bool invert(int m, std::vector<double> a, std::vector<double>& inv) {
+  inv.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(a[(size_t)r * m + c]) > std::fabs(a[(size_t)piv * m + c])) piv = r;
+    if (a[(size_t)piv * m + c] == 0.0) return false;
+    for (int j = 0; j < m; ++j) {
+      std::swap(a[(size_t)c * m + j], a[(size_t)piv * m + j]);
+      std::swap(inv[(size_t)c * m + j], inv[(size_t)piv * m + j]);
+    }
+    const double d = 1.0 / a[(size_t)c * m + c];
+    for (int j = 0; j < m; ++j) {
+      a[(size_t)c * m + j] *= d;
+      inv[(size_t)c * m + j] *= d;
+    }
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * m + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < m; ++j) {
+        a[(size_t)r * m + j] -= f * a[(size_t)c * m + j];
+        inv[(size_t)r * m + j] -= f * inv[(size_t)c * m + j];
+      }
+    }
+  }
+  return true;
+}
+
+template <typename H, typename D>
+int upload(D** dst, const std::vector<H>& src) {
+  std::vector<D> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = D(src[i]);
+  CUDA_TRY(cudaMalloc(dst, tmp.size() * sizeof(D)));
+  CUDA_TRY(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(D), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+int upload_tw(int L, Cplx<double>** d, Cplx<float>** f) {
+  std::vector<Cplx<double>> tw(L);
+  std::vector<Cplx<float>> twf(L);
+  for (int m = 0; m < L; ++m) {
+    const double ang = 2.0 * M_PI * double(m) / double(L);
+    tw[m] = Cplx<double>{std::cos(ang), -std::sin(ang)};
+    twf[m] = Cplx<float>{float(tw[m].re), float(tw[m].im)};
+  }
+  CUDA_TRY(cudaMalloc(d, L * sizeof(Cplx<double>)));
+  CUDA_TRY(cudaMemcpy(*d, tw.data(), L * sizeof(Cplx<double>), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(f, L * sizeof(Cplx<float>)));
+  CUDA_TRY(cudaMemcpy(*f, twf.data(), L * sizeof(Cplx<float>), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+// The cell block A_cc = W_y (x) A1_cc/hx + A1_cc/hy (x) W_x (node index a*n + b), its inverse
+// scaled by sqrt(W) on both sides; the coarse eigenvalues of P^T A P from the 1D cell-average
+// stencil [co, cc, co] (cc = 1^T A1_cc 1, co = (1^T betaA)(1^T lL), per unit h):
+// lambda(kx, ky) = (hy/hx)(cc + 2 co cos(2 pi kx/Nx)) + (hx/hy)(cc + 2 co cos(2 pi ky/Ny)).
+int build_pc(dg_grid* g) {
+  const int n = g->n, NN = n * n;
+  const RefTables& t = g->rt;
+  double wh[kMaxN];
+  for (int j = 0; j < n; ++j) wh[j] = 0.5 * t.w[j];
+  std::vector<double> Acc((size_t)NN * NN, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int a2 = 0; a2 < n; ++a2)
+        for (int b2 = 0; b2 < n; ++b2) {
+          double v = 0.0;
+          if (a == a2) v += g->hy * wh[a] * t.A1cc[b][b2] / g->hx;
+          if (b == b2) v += t.A1cc[a][a2] / g->hy * g->hx * wh[b];
+          Acc[(size_t)(a * n + b) * NN + (a2 * n + b2)] = v;
+        }
+  std::vector<double> inv;
+  if (!invert(NN, Acc, inv)) return fail(DG_ERR_ARG, "cell block of the LDG operator is singular");
+  std::vector<double> sw(NN);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) sw[a * n + b] = std::sqrt(g->hy * wh[a] * g->hx * wh[b]);
+  std::vector<double> Bt((size_t)NN * NN);
+  for (int k = 0; k < NN; ++k)
+    for (int j = 0; j < NN; ++j) Bt[(size_t)k * NN + j] = sw[k] * inv[(size_t)k * NN + j] * sw[j];
+  double cc = 0.0, sb = 0.0, sl = 0.0;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) cc += t.A1cc[i][j];
+    sb += t.betaA[i];
+    sl += t.lL[i];
+  }
+  const double co = sb * sl;
+  std::vector<double> ax(g->Nx), ay(g->Ny);
+  for (int k = 0; k < g->Nx; ++k) ax[k] = (g->hy / g->hx) * (cc + 2.0 * co * std::cos(2.0 * M_PI * k / g->Nx));
+  for (int k = 0; k < g->Ny; ++k) ay[k] = (g->hx / g->hy) * (cc + 2.0 * co * std::cos(2.0 * M_PI * k / g->Ny));
+  PcTables& P = g->pc;
+  if (int rc = upload(&P.Bt, Bt)) return rc;
+  if (int rc = upload(&P.Btf, Bt)) return rc;
+  if (int rc = upload(&P.ax, ax)) return rc;
+  if (int rc = upload(&P.axf, ax)) return rc;
+  if (int rc = upload(&P.ay, ay)) return rc;
+  if (int rc = upload(&P.ayf, ay)) return rc;
+  if (int rc = upload_tw(g->Nx, &P.twx, &P.twxf)) return rc;
+  if (int rc = upload_tw(g->Ny, &P.twy, &P.twyf)) return rc;
+  P.log2x = log2_exact(g->Nx);
+  P.log2y = log2_exact(g->Ny);
+  return DG_OK;
+}
+
+PrecondArgs<double> pc_args(const dg_grid* g, const Workspace& w) {
+  PrecondArgs<double> P{};
+  P.Bt = g->pc.Bt;
+  P.twx = g->pc.twx;
+  P.twy = g->pc.twy;
+  P.ax = g->pc.ax;
+  P.ay = g->pc.ay;
+  P.log2x = g->pc.log2x;
+  P.log2y = g->pc.log2y;
+  P.z = w.pz;
+  P.rc = w.prc;
+  P.uc = w.puc;
+  P.C = w.pC;
+  return P;
+}
+
+PrecondArgs<float> pc_args_f(const dg_grid* g, const Workspace& w) {
+  PrecondArgs<float> P{};
+  P.Bt = g->pc.Btf;
+  P.twx = g->pc.twxf;
+  P.twy = g->pc.twyf;
+  P.ax = g->pc.axf;
+  P.ay = g->pc.ayf;
+  P.log2x = g->pc.log2x;
+  P.log2y = g->pc.log2y;
+  P.z = w.pzf;
+  P.rc = w.prcf;
+  P.uc = w.pucf;
+  P.C = w.pCf;
+  return P;
+}
+
 // ---- launches ---------------------------------------------------------------------------
 
 template <typename T, int N>
@@ -331,7 +531,7 @@ int record_event(std::vector<cudaEvent_t>& pool, size_t& used, cudaStream_t st) 
 template <typename T, int N>
 int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = cg_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  const size_t smem = cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
   auto kern = cg_kernel<T, N>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
@@ -342,6 +542,7 @@ int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st
   A.part = reinterpret_cast<T*>(w.part);
   A.sync = w.sync;
   A.status = w.status;
+  if constexpr (sizeof(T) == 8) A.pc = pc_args(g, w);
   CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
   void* args[] = {(void*)&ops_of<T, N>(g), (void*)&G, (void*)&A};
   const bool tm = timed && timed->timing;
@@ -356,7 +557,7 @@ int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st
 template <int N>
 int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = mixed_smem_bytes<N>(G.TY, G.TX);
+  const size_t smem = mixed_smem_bytes<N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
   auto kern = mixed_cg_kernel<N>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
@@ -366,6 +567,7 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
   grid = std::min(grid, w.grid_cap);
   A.rf = w.rf;
   A.v = CgVectors<float>{w.fe, w.fr, w.fp0, w.fp1, w.fq};
+  A.pc = pc_args_f(g, w);
   A.partd = w.part;
   A.partf = w.partf;
   A.sync = w.sync;
@@ -483,8 +685,12 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
     build_ops<decltype(nc)::value>(g);
     return DG_OK;
   });
-  if (int rc = alloc_ws(g->ws, ndof_of(g), co_resident_cap(g), true)) {
+  int rc = alloc_ws(g->ws, ndof_of(g), co_resident_cap(g), true);
+  if (!rc) rc = alloc_ws_precond(g->ws, (size_t)Nx * Ny, false);
+  if (!rc) rc = build_pc(g);
+  if (rc) {
     free_ws(g->ws);
+    free_pc(g->pc);
     delete g;
     return rc;
   }
@@ -495,7 +701,15 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
 int dg_grid_destroy(dg_grid* g) {
   if (!g) return DG_OK;
   free_ws(g->ws);
+  free_pc(g->pc);
   delete g;
+  return DG_OK;
+}
+
+int dg_grid_set_precond(dg_grid* g, int kind) {
+  if (!g) return fail(DG_ERR_ARG, "g is NULL");
+  if (kind != DG_PRECOND_JACOBI && kind != DG_PRECOND_TWOLEVEL) return fail(DG_ERR_ARG, "unknown preconditioner %d", kind);
+  g->precond = kind;
   return DG_OK;
 }
 
@@ -565,6 +779,7 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
   A.ca = 1.0;
   A.x_unscaled = 1;
   A.v = CgVectors<double>{g->ws.y, g->ws.r, g->ws.p0, g->ws.p1, g->ws.q};
+  A.precond = g->precond;
   A.psi_out = psi;
   A.tol2 = tol * tol;
   A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
@@ -633,6 +848,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.cb = cb;
     A.x_unscaled = 0;
     A.y = y;
+    A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
     A.tol_in2 = s->tol_in * s->tol_in;
     A.max_sweeps = s->max_sweeps;
@@ -648,6 +864,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.cb = cb;
     A.x_unscaled = 0;
     A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
+    A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
     A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
     A.fixed_iters = s->fixed_iters;
@@ -831,6 +1048,7 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
     CUDA_TRY(cudaMalloc(&s->k2, rbytes));
     CUDA_TRY(cudaMalloc(&s->k3, rbytes));
     if (int rc = alloc_ws(s->ws, ndof_of(g), co_resident_cap(g), false)) return rc;
+    if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision == DG_MIXED)) return rc;
     return precision == DG_MIXED ? alloc_ws_mixed(s->ws) : DG_OK;
   };
   int rc = alloc_all();

@@ -238,4 +238,65 @@ __device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag) {
   return *s_flag == 0;
 }
 
+// ---- lines of a 2D DFT in shared memory ---------------------------------------------------
+
+template <typename T>
+struct Cplx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
+  return Cplx<T>{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+
+// In-place DFT of one line of length L held in shared memory s[0..L), computed by the
+// whole block.  tw[m] = exp(-2 pi i m / L), m < L (host-computed).  inverse: conjugate
+// twiddles (no 1/L factor).  Power-of-two L: iterative radix-2 decimation in time on
+// bit-reversed input (the caller loads s[bitrev(j)] = x[j]); otherwise a direct O(L^2) sum
+// into tmp[0..L) copied back.
+template <typename T>
+__device__ __forceinline__ void dft_line(Cplx<T>* s, Cplx<T>* tmp, int L, int log2L, const Cplx<T>* tw,
+                                         bool inverse) {
+  if (log2L >= 0) {
+    for (int half = 1; half < L; half <<= 1) {
+      const int stride = L / (2 * half);
+      for (int t = threadIdx.x; t < L / 2; t += blockDim.x) {
+        const int grp = t / half, pos = t - (t / half) * half;
+        const int i1 = grp * 2 * half + pos, i2 = i1 + half;
+        Cplx<T> w = tw[pos * stride];
+        if (inverse) w.im = -w.im;
+        const Cplx<T> u = s[i1];
+        const Cplx<T> v = cmul(w, s[i2]);
+        s[i1] = Cplx<T>{u.re + v.re, u.im + v.im};
+        s[i2] = Cplx<T>{u.re - v.re, u.im - v.im};
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+      T re = T(0), im = T(0);
+      int m = 0;  // (j * k) mod L, advanced incrementally
+      for (int j = 0; j < L; ++j) {
+        Cplx<T> w = tw[m];
+        if (inverse) w.im = -w.im;
+        const Cplx<T> v = cmul(w, s[j]);
+        re += v.re;
+        im += v.im;
+        m += k;
+        if (m >= L) m -= L;
+      }
+      tmp[k] = Cplx<T>{re, im};
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < L; k += blockDim.x) s[k] = tmp[k];
+    __syncthreads();
+  }
+}
+
+// Position of element j of a line in the shared buffer before dft_line.
+__device__ __forceinline__ int dft_slot(int j, int log2L) {
+  return log2L > 0 ? int(__brev(unsigned(j)) >> (32 - log2L)) : j;
+}
+
 }  // namespace dgk

@@ -248,32 +248,6 @@ struct CgVectors {
   T* q;      // Ahat p
 };
 
-// One CG tile pass: stage u = load(...) (plus-shaped halo), apply Ahat, hand (g, k, u, q)
-// to out(...).
-template <typename T, int N, class LoadF, class OutF>
-__device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& G, int tile, T* sU, T* tXR,
-                                              T* tXL, T* tYR, T* tYL, LoadF&& load, OutF&& out) {
-  constexpr int NN = N * N;
-  const TileBox B = make_box(G, tile);
-  stage_box<T, N>(G, B, sU, false, load);
-  __syncthreads();
-  line_traces<T, N>(B, sU, sU, C.kx, C.ky, tXR, tXL, tYR, tYL, false);
-  __syncthreads();
-  const int nin = B.TYe * B.TXe * NN;
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-    const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const int lc = (ry + 1) * B.BW + rx + 1;
-    const int a = k / N, b = k - (k / N) * N;
-    const T q = op_x_at<T, N>(sU, tXR, tXL, C.kx, lc, a, b) + op_y_at<T, N>(sU, tYR, tYL, C.ky, lc, B.BW, a, b);
-    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-    out(g, k, sU[lc * NN + k], q);
-  }
-  __syncthreads();
-}
-
-// Right-hand side of the scaled system at node k of global offset g:
-//   b = rhs[g] if rhs is given, else sqrt(W_k) (omega[g] - wbar).
 template <typename T>
 struct RhsSource {
   const double* omega;
@@ -289,16 +263,220 @@ __device__ __forceinline__ T rhs_at(const Ops2D<T, N>& C, const RhsSource<T>& B,
 // Restarts from the true residual allowed after the recursive one has met the tolerance.
 constexpr int kMaxRestarts = 20;
 
-// The CG iterations proper, from r (residual of the current y) with rho = r.r, rhob = b.b.
-// The stopping rule is on the true residual: when the recursive residual meets the
-// tolerance, one more tile pass computes b - Ahat y; if that misses the tolerance, CG
-// restarts from it (p = r).  Returns the iteration count; raises flags.
-// part: 4 * gridDim.x values of scratch.
+// ---- the two-level preconditioner --------------------------------------------------------
+// In the scaled space (r~ = W^-1/2 r) the preconditioner M^-1 = B + P A_c^+ P^T of the
+// unscaled system reads  z~ = Bt r~ + sqrt(W) (A_c^+ rc),  rc = sum over a cell's nodes of
+// sqrt(W) r~  (= P^T r),  Bt = diag(sqrt W) A_cc^-1 diag(sqrt W)  (one n^2 x n^2 matrix for
+// every cell), A_c = P^T A P the Galerkin coarse operator on the cells, diagonalised by the
+// 2D DFT with eigenvalues ax[kx] + ay[ky] (constant mode dropped).
+template <typename T>
+struct PrecondArgs {
+  const T* Bt;          // N^2 x N^2, row-major
+  const Cplx<T>* twx;   // exp(-2 pi i m / Nx), m < Nx
+  const Cplx<T>* twy;   // exp(-2 pi i m / Ny), m < Ny
+  const T* ax;          // coarse eigenvalues: lambda(kx, ky) = ax[kx] + ay[ky]
+  const T* ay;
+  int log2x, log2y;     // log2 of Nx, Ny when powers of two, else -1 (direct DFT)
+  T* z;                 // cell-block part of z~ (one value per dof)
+  T* rc;                // restricted residual (one per cell)
+  T* uc;                // coarse correction (one per cell)
+  Cplx<T>* C;           // coarse spectrum (Ny x Nx)
+};
+
+// Shared memory and synchronisation of one persistent solve.
+template <typename T>
+struct SolveCtx {
+  T *sU, *tXR, *tXL, *tYR, *tYL;  // tile staging
+  Cplx<T>* line0;                 // DFT line buffers (alias the tile staging)
+  Cplx<T>* line1;
+  const T* Bs;                    // Bt staged in shared memory (null without preconditioner)
+  T* red;
+  T* bcast;
+  int* s_flag;
+  SyncState* sync;
+  T* part;                        // 4 * gridDim.x: two alternating halves
+  int phase;
+};
+
+// Block partials of one or two sums -> grid barrier -> the sums in every block (fixed order).
+template <typename T>
+__device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
+  T* ph = X.part + (X.phase & 1) * 2 * gridDim.x;
+  ++X.phase;
+  v0 = block_sum(v0, X.red);
+  if (threadIdx.x == 0) __stcg(ph + blockIdx.x, v0);
+  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  out0 = sum_partials(ph, gridDim.x, 1, X.bcast);
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0, T& out1) {
+  T* ph = X.part + (X.phase & 1) * 2 * gridDim.x;
+  ++X.phase;
+  v0 = block_sum(v0, X.red);
+  if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, v0);
+  v1 = block_sum(v1, X.red);
+  if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, v1);
+  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  out0 = sum_partials(ph, gridDim.x, 2, X.bcast);
+  out1 = sum_partials(ph + 1, gridDim.x, 2, X.bcast);
+  return true;
+}
+
+// One CG tile pass: stage u = load(...) (plus-shaped halo), apply Ahat, hand (g, k, u, q)
+// to out(...).
+template <typename T, int N, class LoadF, class OutF>
+__device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& G, int tile, SolveCtx<T>& X,
+                                              LoadF&& load, OutF&& out) {
+  constexpr int NN = N * N;
+  const TileBox B = make_box(G, tile);
+  stage_box<T, N>(G, B, X.sU, false, load);
+  __syncthreads();
+  line_traces<T, N>(B, X.sU, X.sU, C.kx, C.ky, X.tXR, X.tXL, X.tYR, X.tYL, false);
+  __syncthreads();
+  const int nin = B.TYe * B.TXe * NN;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int lc = (ry + 1) * B.BW + rx + 1;
+    const int a = k / N, b = k - (k / N) * N;
+    const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
+                op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
+    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+    out(g, k, X.sU[lc * NN + k], q);
+  }
+  __syncthreads();
+}
+
+// Cell part of the preconditioner on one tile whose interior residual is staged in X.sU:
+// z~ = Bt r~ on every cell, rc = sum sqrt(W) r~ per cell; returns the tile's r~ . z~_block.
+template <typename T, int N>
+__device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const TileBox& B,
+                                      const PrecondArgs<T>& P, SolveCtx<T>& X) {
+  constexpr int NN = N * N;
+  T rz = T(0);
+  const int nin = B.TYe * B.TXe * NN;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int c = i / NN, k = i - (i / NN) * NN;
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * NN;
+    T zj = T(0);
+#pragma unroll
+    for (int j = 0; j < NN; ++j) zj = fma(X.Bs[k * NN + j], u[j], zj);
+    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+    __stcg(P.z + g, zj);
+    rz = fma(u[k], zj, rz);
+  }
+  const int ncell = B.TYe * B.TXe;
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * NN;
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < NN; ++k) v = fma(C.sw[k], u[k], v);
+    const size_t cell = (size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx);
+    __stcg(P.rc + cell, v);
+    __stcg(&P.C[cell].re, v);
+    __stcg(&P.C[cell].im, T(0));
+  }
+  return rz;
+}
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> ld_cplx(const Cplx<T>* p) {
+  return Cplx<T>{__ldcg(&p->re), __ldcg(&p->im)};
+}
+
+template <typename T>
+__device__ __forceinline__ void st_cplx(Cplx<T>* p, Cplx<T> v) {
+  __stcg(&p->re, v.re);
+  __stcg(&p->im, v.im);
+}
+
+// Coarse solve uc = A_c^+ rc from the spectrum array C (holding rc): forward DFT of the rows,
+// per column forward DFT, division by the eigenvalues, inverse DFT, then inverse DFT of the
+// rows.  Three grid-wide phases.  Returns sum uc . rc (in every block).
+template <typename T>
+__device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P, SolveCtx<T>& X, T& ucrc) {
+  const int Nx = G.Nx, Ny = G.Ny;
+  for (int row = blockIdx.x; row < Ny; row += gridDim.x) {
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
+    __syncthreads();
+    dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, false);
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) st_cplx(&P.C[(size_t)row * Nx + j], X.line0[j]);
+    __syncthreads();
+  }
+  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  const T scale = T(1) / (T(Nx) * T(Ny));
+  for (int col = blockIdx.x; col < Nx; col += gridDim.x) {
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) X.line0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * Nx + col]);
+    __syncthreads();
+    dft_line(X.line0, X.line1, Ny, P.log2y, P.twy, false);
+    for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
+      const T f = (col == 0 && ky == 0) ? T(0) : scale / (P.ax[col] + P.ay[ky]);
+      const Cplx<T> v = X.line0[ky];
+      X.line1[dft_slot(ky, P.log2y)] = Cplx<T>{v.re * f, v.im * f};
+    }
+    __syncthreads();
+    dft_line(X.line1, X.line0, Ny, P.log2y, P.twy, true);
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * Nx + col], X.line1[j]);
+    __syncthreads();
+  }
+  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  T acc = T(0);
+  for (int row = blockIdx.x; row < Ny; row += gridDim.x) {
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
+    __syncthreads();
+    dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, true);
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
+      const size_t cell = (size_t)row * Nx + j;
+      const T u = X.line0[j].re;
+      __stcg(P.uc + cell, u);
+      acc = fma(u, __ldcg(P.rc + cell), acc);
+    }
+    __syncthreads();
+  }
+  return reduce_all(X, acc, ucrc);
+}
+
+// z~ = M^-1 r~ for the residual currently in r; returns r~ . z~ in rz.
+template <typename T, int N>
+__device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, const PrecondArgs<T>& P, const T* r,
+                                         SolveCtx<T>& X, T& rz) {
+  constexpr int NN = N * N;
+  const int ntiles = G.tilesX * G.tilesY;
+  T rzb = T(0);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileBox B = make_box(G, t);
+    const int nin = B.TYe * B.TXe * NN;
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+      const int c = i / NN, k = i - (i / NN) * NN;
+      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+      X.sU[((ry + 1) * B.BW + rx + 1) * NN + k] = __ldcg(r + g);
+    }
+    __syncthreads();
+    rzb += pc_cells<T, N>(C, G, B, P, X);
+    __syncthreads();
+  }
+  T rzsum = T(0);
+  if (!reduce_all(X, rzb, rzsum)) return false;
+  T ucrc = T(0);
+  if (!pc_coarse(G, P, X, ucrc)) return false;
+  rz = rzsum + ucrc;
+  return true;
+}
+
+// The CG iterations proper (PCG when P is non-null), from r (residual of the current y) with
+// rr = r.r, rhob = b.b (the stopping rule is on r.r) and, with a preconditioner, z = M^-1 r
+// already applied and rz = r.z.  The stopping rule is on the true residual: when the
+// recursive residual meets the tolerance, one more tile pass computes b - Ahat y; if that
+// misses the tolerance, CG restarts from it.  Returns the iteration count; raises flags.
 template <typename T, int N>
 __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, const CgVectors<T>& V,
-                                          const RhsSource<T>& Bsrc, T* part, int& phase, SyncState* sync,
-                                          int* s_flag, T* sU, T* tXR, T* tXL, T* tYR, T* tYL, T* red, T* bcast,
-                                          T& rho, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
+                                          const PrecondArgs<T>* P, const RhsSource<T>& Bsrc, SolveCtx<T>& X,
+                                          T& rr, T rz, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
                                           int max_restarts = kMaxRestarts) {
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
@@ -307,57 +485,62 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
   int it = 0, restarts = 0;
   T beta = T(0);
   int cur = 0;
-  bool first = true;  // p = r (no previous direction)
+  bool first = true;  // p = z (no previous direction)
+  if (!P) rz = rr;
   while (true) {
     if (fixed_iters > 0) {
       if (it >= fixed_iters) break;
-    } else if (double(rho) <= tol2 * double(rhob)) {
+    } else if (double(rr) <= tol2 * double(rhob)) {
       if (max_restarts == 0) break;  // loose inner solves: the recursive residual suffices
       // Verify on the true residual r = b - Ahat y.
       T rt = T(0);
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         cg_tile_apply<T, N>(
-            C, G, t, sU, tXR, tXL, tYR, tYL, [&](size_t g, int, bool) { return __ldcg(V.y + g); },
+            C, G, t, X, [&](size_t g, int, bool) { return __ldcg(V.y + g); },
             [&](size_t g, int k, T, T qv) {
               const T r = rhs_at<T, N>(C, Bsrc, g, k) - qv;
               __stcg(V.r + g, r);
               rt = fma(r, r, rt);
             });
       }
-      T* ph = part + (phase & 1) * 2 * gridDim.x;
-      ++phase;
-      rt = block_sum(rt, red);
-      if (threadIdx.x == 0) __stcg(ph + blockIdx.x, rt);
-      if (!grid_barrier(sync, s_flag)) {
+      T rr_true = T(0);
+      if (!reduce_all(X, rt, rr_true)) {
         flags |= kFlagTimeout;
         return it;
       }
-      const T rho_true = sum_partials(ph, gridDim.x, 1, bcast);
-      rho = rho_true;
-      if (double(rho_true) <= tol2 * double(rhob)) break;
+      rr = rr_true;
+      if (double(rr_true) <= tol2 * double(rhob)) break;
       if (restarts >= max_restarts) {
         flags |= kFlagNoconv;
         break;
       }
       ++restarts;
+      if (P) {
+        if (!pc_apply<T, N>(C, G, *P, V.r, X, rz)) {
+          flags |= kFlagTimeout;
+          return it;
+        }
+      } else {
+        rz = rr;
+      }
       first = true;
       continue;
     }
-    if (rho == T(0)) break;
+    if (rr == T(0)) break;
     if (it >= maxit) {
       flags |= kFlagNoconv;
       break;
     }
     T* pin = cur ? V.p1 : V.p0;
     T* pout = cur ? V.p0 : V.p1;
-    // Phase A: p = r + beta p_old (halo recomputed locally), q = Ahat p, p.q.
+    // Phase A: p = z + beta p_old (halo recomputed locally), q = Ahat p, p.q.
     T pq = T(0);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       cg_tile_apply<T, N>(
-          C, G, t, sU, tXR, tXL, tYR, tYL,
-          [&](size_t g, int, bool interior) {
-            const T rv = __ldcg(V.r + g);
-            const T pv = first ? rv : fma(beta, __ldcg(pin + g), rv);
+          C, G, t, X,
+          [&](size_t g, int k, bool interior) {
+            const T zv = P ? fma(C.sw[k], __ldcg(P->uc + g / NN), __ldcg(P->z + g)) : __ldcg(V.r + g);
+            const T pv = first ? zv : fma(beta, __ldcg(pin + g), zv);
             if (interior) __stcg(pout + g, pv);
             return pv;
           },
@@ -366,46 +549,89 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
             pq = fma(pv, qv, pq);
           });
     }
-    T* ph = part + (phase & 1) * 2 * gridDim.x;
-    ++phase;
-    pq = block_sum(pq, red);
-    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, pq);
-    if (!grid_barrier(sync, s_flag)) {
+    T pqs = T(0);
+    if (!reduce_all(X, pq, pqs)) {
       flags |= kFlagTimeout;
       return it;
     }
-    const T pqs = sum_partials(ph, gridDim.x, 1, bcast);
     if (!(pqs > T(0))) {
       flags |= kFlagBreakdown;
       break;
     }
-    const T alpha = rho / pqs;
-    // Phase B: y += alpha p, r -= alpha q, r.r  (pointwise, grid-stride).
-    T rr = T(0);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) {
-      const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
-      const T yv = fma(alpha, pv, __ldcg(V.y + i));
-      const T rv = fma(-alpha, qv, __ldcg(V.r + i));
-      __stcg(V.y + i, yv);
-      __stcg(V.r + i, rv);
-      rr = fma(rv, rv, rr);
+    const T alpha = rz / pqs;
+    // Phase B: y += alpha p, r -= alpha q, r.r (and the cell part of the preconditioner).
+    T rrb = T(0), rzb = T(0);
+    if (!P) {
+      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) {
+        const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
+        const T yv = fma(alpha, pv, __ldcg(V.y + i));
+        const T rv = fma(-alpha, qv, __ldcg(V.r + i));
+        __stcg(V.y + i, yv);
+        __stcg(V.r + i, rv);
+        rrb = fma(rv, rv, rrb);
+      }
+    } else {
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileBox B = make_box(G, t);
+        const int nin = B.TYe * B.TXe * NN;
+        for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+          const int c = i / NN, k = i - (i / NN) * NN;
+          const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+          const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+          const T pv = __ldcg(pout + g), qv = __ldcg(V.q + g);
+          const T yv = fma(alpha, pv, __ldcg(V.y + g));
+          const T rv = fma(-alpha, qv, __ldcg(V.r + g));
+          __stcg(V.y + g, yv);
+          __stcg(V.r + g, rv);
+          rrb = fma(rv, rv, rrb);
+          X.sU[((ry + 1) * B.BW + rx + 1) * NN + k] = rv;
+        }
+        __syncthreads();
+        rzb += pc_cells<T, N>(C, G, B, *P, X);
+        __syncthreads();
+      }
     }
-    ph = part + (phase & 1) * 2 * gridDim.x;
-    ++phase;
-    rr = block_sum(rr, red);
-    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, rr);
-    if (!grid_barrier(sync, s_flag)) {
+    T rnew = T(0), rzjs = T(0);
+    if (!reduce_all2(X, rrb, rzb, rnew, rzjs)) {
       flags |= kFlagTimeout;
       return it;
     }
-    const T rnew = sum_partials(ph, gridDim.x, 1, bcast);
-    beta = rnew / rho;
-    rho = rnew;
+    T rznew = rnew;
+    if (P) {
+      T ucrc = T(0);
+      if (!pc_coarse(G, *P, X, ucrc)) {
+        flags |= kFlagTimeout;
+        return it;
+      }
+      rznew = rzjs + ucrc;
+    }
+    beta = rznew / rz;
+    rz = rznew;
+    rr = rnew;
     cur ^= 1;
     first = false;
     ++it;
   }
   return it;
+}
+
+// Removes the W-mean of psi = y / sqrt(W) from y (y -= m sqrt(W)): a preconditioner other
+// than W^-1 moves the iterates along the constants, the kernel of A.
+template <typename T, int N>
+__device__ __forceinline__ bool project_mean(const Ops2D<T, N>& C, const Geom& G, T* y, double sumW,
+                                             SolveCtx<T>& X) {
+  constexpr int NN = N * N;
+  const size_t ndof = (size_t)G.Nx * G.Ny * NN;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  T s = T(0);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    s = fma(C.sw[i % NN], __ldcg(y + i), s);
+  T m = T(0);
+  if (!reduce_all(X, s, m)) return false;
+  m = m / T(sumW);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    __stcg(y + i, fma(-m, C.sw[i % NN], __ldcg(y + i)));
+  return grid_barrier(X.sync, X.s_flag);
 }
 
 template <typename T>
@@ -417,6 +643,8 @@ struct CgArgs {
   double ca, cb;
   int x_unscaled;
   CgVectors<T> v;
+  int precond;          // 0: W^-1 (plain CG on the scaled system), 1: two-level
+  PrecondArgs<T> pc;
   double* psi_out;      // if non-null: psi = y / sqrt(W) at the end
   T* part;              // 4 * gridDim.x
   SyncState* sync;
@@ -426,9 +654,46 @@ struct CgArgs {
   double sumW;
 };
 
+// Dynamic shared memory of the persistent solves: [Bt (with the preconditioner)] then one
+// region used both for the tile staging and for two DFT lines.
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 template <typename T, int N>
-__host__ __device__ constexpr size_t cg_smem_values(int TY, int TX) {
+__host__ __device__ constexpr size_t cg_tile_values(int TY, int TX) {
   return (size_t)(TY + 2) * (TX + 2) * (N * N + 4 * N);
+}
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t cg_smem_bytes(int TY, int TX, int Lmax, bool pc) {
+  return (pc ? align16(sizeof(T) * N * N * N * N) : 0) +
+         align16(cg_tile_values<T, N>(TY, TX) * sizeof(T) > (pc ? 2 * (size_t)Lmax * sizeof(Cplx<T>) : 0)
+                     ? cg_tile_values<T, N>(TY, TX) * sizeof(T)
+                     : 2 * (size_t)Lmax * sizeof(Cplx<T>));
+}
+
+// Lays out the solve context over dynamic shared memory starting at base (bytes).
+template <typename T, int N>
+__device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, const Geom& G, const T* Bt_global,
+                                         bool pc, int Lmax) {
+  constexpr int NN = N * N;
+  unsigned char* p = base;
+  if (pc) {
+    T* Bs = reinterpret_cast<T*>(p);
+    for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) Bs[i] = Bt_global[i];
+    X.Bs = Bs;
+    p += align16(sizeof(T) * NN * NN);
+  } else {
+    X.Bs = nullptr;
+  }
+  const int boxc = (G.TY + 2) * (G.TX + 2);
+  X.sU = reinterpret_cast<T*>(p);
+  X.tXR = X.sU + boxc * NN;
+  X.tXL = X.tXR + boxc * N;
+  X.tYR = X.tXL + boxc * N;
+  X.tYL = X.tYR + boxc * N;
+  X.line0 = reinterpret_cast<Cplx<T>*>(p);
+  X.line1 = X.line0 + Lmax;
+  __syncthreads();
 }
 
 template <typename T, int N>
@@ -436,17 +701,23 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
                                                      const __grid_constant__ CgArgs<T> A) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sU = reinterpret_cast<T*>(smem_raw);
-  const int boxc = (G.TY + 2) * (G.TX + 2);
-  T *tXR = sU + boxc * NN, *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
   __shared__ T red[32];
   __shared__ T bcast;
   __shared__ int s_flag;
+  const bool pc = A.precond == 1;
+  SolveCtx<T> X;
+  init_ctx<T, N>(X, smem_raw, G, A.pc.Bt, pc, max(G.Nx, G.Ny));
+  X.red = red;
+  X.bcast = &bcast;
+  X.s_flag = &s_flag;
+  X.sync = A.sync;
+  X.part = A.part;
+  X.phase = 0;
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  int phase = 0, flags = 0, it = 0;
-  T rho = T(0), rhob = T(0);
+  int flags = 0, it = 0;
+  T rr = T(0), rhob = T(0), rz = T(0);
 
   // P0: W-mean of omega, in two passes (the second removes the rounding left by the first,
   // so that b carries no rounding-sized component along the kernel of A).
@@ -456,23 +727,20 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
       T s = T(0);
       for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
         s = fma(C.wq[i % NN], T(A.omega[i]) - wbar, s);
-      T* ph = A.part + (phase & 1) * 2 * gridDim.x;
-      ++phase;
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) __stcg(ph + blockIdx.x, s);
-      if (!grid_barrier(A.sync, &s_flag)) {
+      T m = T(0);
+      if (!reduce_all(X, s, m)) {
         flags |= kFlagTimeout;
         goto finish;
       }
-      wbar += sum_partials(ph, gridDim.x, 1, &bcast) / T(A.sumW);
+      wbar += m / T(A.sumW);
     }
   }
-  // P1: y0, b, r0 = b - Ahat y0, rho0 = r0.r0, rhob = b.b.
+  // P1: y0, b, r0 = b - Ahat y0, rr0 = r0.r0, rhob = b.b.
   {
-    T rr = T(0), bb = T(0);
+    T rrb = T(0), bbb = T(0);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       cg_tile_apply<T, N>(
-          C, G, t, sU, tXR, tXL, tYR, tYL,
+          C, G, t, X,
           [&](size_t g, int k, bool interior) {
             double v = 0.0;
             if (A.xa) v = A.ca * A.xa[g];
@@ -485,29 +753,26 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
             const T b = rhs_at<T, N>(C, RhsSource<T>{A.omega, A.rhs, wbar}, g, k);
             const T r = b - qv;
             __stcg(A.v.r + g, r);
-            rr = fma(r, r, rr);
-            bb = fma(b, b, bb);
+            rrb = fma(r, r, rrb);
+            bbb = fma(b, b, bbb);
           });
     }
-    T* ph = A.part + (phase & 1) * 2 * gridDim.x;
-    ++phase;
-    rr = block_sum(rr, red);
-    if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, rr);
-    bb = block_sum(bb, red);
-    if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, bb);
-    if (!grid_barrier(A.sync, &s_flag)) {
+    if (!reduce_all2(X, rrb, bbb, rr, rhob)) {
       flags |= kFlagTimeout;
       goto finish;
     }
-    rho = sum_partials(ph, gridDim.x, 2, &bcast);
-    rhob = sum_partials(ph + 1, gridDim.x, 2, &bcast);
   }
   if (rhob == T(0)) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.v.y + i, T(0));
-    rho = T(0);
+    rr = T(0);
   } else {
-    it = cg_iterate<T, N>(C, G, A.v, RhsSource<T>{A.omega, A.rhs, wbar}, A.part, phase, A.sync, &s_flag, sU,
-                          tXR, tXL, tYR, tYL, red, &bcast, rho, rhob, A.tol2, A.maxit, A.fixed_iters, flags);
+    if (pc && !pc_apply<T, N>(C, G, A.pc, A.v.r, X, rz)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+    it = cg_iterate<T, N>(C, G, A.v, pc ? &A.pc : nullptr, RhsSource<T>{A.omega, A.rhs, wbar}, X, rr, rz, rhob,
+                          A.tol2, A.maxit, A.fixed_iters, flags);
+    if (pc && !(flags & kFlagTimeout) && !project_mean<T, N>(C, G, A.v.y, A.sumW, X)) flags |= kFlagTimeout;
   }
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
@@ -523,7 +788,7 @@ finish:
     st->flags |= flags;
     st->nsolves += 1;
     st->last_sweeps = 0;
-    st->last_rho = double(rho);
+    st->last_rho = double(rr);
     st->last_rhob = double(rhob);
   }
 }
@@ -546,6 +811,8 @@ struct MixedArgs {
   double* psi_out;     // if non-null: psi = y / sqrt(W) at the end
   float* rf;           // float32 copy of the float64 residual (inner right-hand side)
   CgVectors<float> v;  // inner solve: y = e, r, p0, p1, q
+  int precond;         // 0: W^-1, 1: two-level (inner float32 solve)
+  PrecondArgs<float> pc;
   double* partd;       // 4 * gridDim.x
   float* partf;        // 4 * gridDim.x
   SyncState* sync;
@@ -556,20 +823,23 @@ struct MixedArgs {
 };
 
 template <int N>
-__host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX) {
-  return cg_smem_values<double, N>(TY, TX) * sizeof(double);
+__host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX, int Lmax, bool pc) {
+  return (pc ? align16(sizeof(float) * N * N * N * N) : 0) +
+         align16(cg_tile_values<double, N>(TY, TX) * sizeof(double) > 2 * (size_t)Lmax * sizeof(Cplx<float>)
+                     ? cg_tile_values<double, N>(TY, TX) * sizeof(double)
+                     : 2 * (size_t)Lmax * sizeof(Cplx<float>));
 }
 
-// One float64 residual pass: r = b - Ahat y (y staged with halo), rf = float(r), inner
-// residual = rf, e = 0.  Returns this block's r.r and b.b.
+// One float64 residual pass: r = b - Ahat y (y staged with halo; pass 0: y = y0), rf =
+// float(r), inner residual = rf, e = 0.  Accumulates this block's r.r and b.b.
 template <int N>
 __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const Geom& G, const MixedArgs& A,
-                                               double wbar, bool from_x0, double* sU, double* tXR, double* tXL,
-                                               double* tYR, double* tYL, double& rr, double& bb) {
+                                               double wbar, bool from_x0, SolveCtx<double>& X, double& rr,
+                                               double& bb) {
   const int ntiles = G.tilesX * G.tilesY;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     cg_tile_apply<double, N>(
-        Cd, G, t, sU, tXR, tXL, tYR, tYL,
+        Cd, G, t, X,
         [&](size_t g, int k, bool interior) {
           if (!from_x0) return __ldcg(A.y + g);
           double v = 0.0;
@@ -598,52 +868,54 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
                                                            const __grid_constant__ MixedArgs A) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int boxc = (G.TY + 2) * (G.TX + 2);
-  double* sUd = reinterpret_cast<double*>(smem_raw);
-  double *tXRd = sUd + boxc * NN, *tXLd = tXRd + boxc * N, *tYRd = tXLd + boxc * N, *tYLd = tYRd + boxc * N;
-  float* sUf = reinterpret_cast<float*>(smem_raw);
-  float *tXRf = sUf + boxc * NN, *tXLf = tXRf + boxc * N, *tYRf = tXLf + boxc * N, *tYLf = tYRf + boxc * N;
   __shared__ double redd[32];
   __shared__ double bcd;
   __shared__ float redf[32];
   __shared__ float bcf;
   __shared__ int s_flag;
+  const bool pc = A.precond == 1;
+  const int Lmax = max(G.Nx, G.Ny);
+  SolveCtx<float> Xf;
+  init_ctx<float, N>(Xf, smem_raw, G, A.pc.Bt, pc, Lmax);
+  Xf.red = redf;
+  Xf.bcast = &bcf;
+  Xf.s_flag = &s_flag;
+  Xf.sync = A.sync;
+  Xf.part = A.partf;
+  Xf.phase = 0;
+  SolveCtx<double> Xd;
+  init_ctx<double, N>(Xd, smem_raw + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
+  Xd.red = redd;
+  Xd.bcast = &bcd;
+  Xd.s_flag = &s_flag;
+  Xd.sync = A.sync;
+  Xd.part = A.partd;
+  Xd.phase = 0;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  int phase = 0, flags = 0, sweeps = 0;
+  int flags = 0, sweeps = 0;
   long long inner = 0;
   double rr = 0.0, bb = 0.0, wbar = 0.0;
   for (int mp = 0; mp < 2; ++mp) {  // two-pass W-mean, as in cg_kernel
     double s = 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
       s = fma(Cd.wq[i % NN], A.omega[i] - wbar, s);
-    double* ph = A.partd + (phase & 1) * 2 * gridDim.x;
-    ++phase;
-    s = block_sum(s, redd);
-    if (threadIdx.x == 0) __stcg(ph + blockIdx.x, s);
-    if (!grid_barrier(A.sync, &s_flag)) {
+    double m = 0.0;
+    if (!reduce_all(Xd, s, m)) {
       flags |= kFlagTimeout;
       goto finish;
     }
-    wbar += sum_partials(ph, gridDim.x, 1, &bcd) / A.sumW;
+    wbar += m / A.sumW;
   }
   for (int pass = 0;; ++pass) {
     // float64 residual of the current iterate (pass 0: of the initial guess)
     {
       double r2 = 0.0, b2 = 0.0;
-      mixed_residual<N>(Cd, G, A, wbar, pass == 0, sUd, tXRd, tXLd, tYRd, tYLd, r2, b2);
-      double* ph = A.partd + (phase & 1) * 2 * gridDim.x;
-      ++phase;
-      r2 = block_sum(r2, redd);
-      if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, r2);
-      b2 = block_sum(b2, redd);
-      if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, b2);
-      if (!grid_barrier(A.sync, &s_flag)) {
+      mixed_residual<N>(Cd, G, A, wbar, pass == 0, Xd, r2, b2);
+      if (!reduce_all2(Xd, r2, b2, rr, bb)) {
         flags |= kFlagTimeout;
         goto finish;
       }
-      rr = sum_partials(ph, gridDim.x, 2, &bcd);
-      bb = sum_partials(ph + 1, gridDim.x, 2, &bcd);
     }
     if (bb == 0.0) {
       for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.y + i, 0.0);
@@ -655,13 +927,17 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
       flags |= kFlagNoconv;
       break;
     }
-    // float32 inner CG from e = 0 on the residual equation
+    // float32 inner (P)CG from e = 0 on the residual equation
     float rho_in = float(rr);
     const float rhob_in = rho_in;
+    float rz_in = rho_in;
+    if (pc && !pc_apply<float, N>(Cf, G, A.pc, A.v.r, Xf, rz_in)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
     int fin = 0;
-    const int it_in = cg_iterate<float, N>(Cf, G, A.v, RhsSource<float>{nullptr, A.rf, 0.0f}, A.partf, phase, A.sync,
-                                           &s_flag, sUf, tXRf, tXLf, tYRf, tYLf, redf, &bcf, rho_in, rhob_in,
-                                           A.tol_in2, A.maxit_in, 0, fin, 0);
+    const int it_in = cg_iterate<float, N>(Cf, G, A.v, pc ? &A.pc : nullptr, RhsSource<float>{nullptr, A.rf, 0.0f},
+                                           Xf, rho_in, rz_in, rhob_in, A.tol_in2, A.maxit_in, 0, fin, 0);
     inner += it_in;
     if (fin & kFlagTimeout) {
       flags |= kFlagTimeout;
@@ -676,6 +952,7 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
     }
     ++sweeps;
   }
+  if (pc && !(flags & kFlagTimeout) && !project_mean<double, N>(Cd, G, A.y, A.sumW, Xd)) flags |= kFlagTimeout;
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)

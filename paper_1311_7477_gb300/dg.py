@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(7)
 DG_FP64, DG_MIXED = 0, 1
+DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
 
 ERROR_NAMES = {DG_ERR_ARG: "DG_ERR_ARG", DG_ERR_CUDA: "DG_ERR_CUDA", DG_ERR_NOMEM: "DG_ERR_NOMEM",
                DG_ERR_NOCONV: "DG_ERR_NOCONV", DG_ERR_NONFINITE: "DG_ERR_NONFINITE",
@@ -54,6 +55,7 @@ def _load():
         "dg_grid_dof": (LL, [P]),
         "dg_grid_nodes": (I, [P, PD, PD, PD]),
         "dg_grid_set_tiles": (I, [P, I, I]),
+        "dg_grid_set_precond": (I, [P, I]),
         "dg_bracket": (I, [P, P, P, P, P]),
         "dg_laplace_apply": (I, [P, P, P, I, P]),
         "dg_poisson_solve": (I, [P, P, P, D, I, I, PI, PD, P]),
@@ -175,6 +177,12 @@ class Grid:
 
     def set_tiles(self, TY, TX):
         _check(_lib.dg_grid_set_tiles(self.h, int(TY), int(TX)))
+
+    def set_precond(self, kind):
+        """DG_PRECOND_JACOBI (W^-1) or DG_PRECOND_TWOLEVEL; also accepts "jacobi" / "twolevel"."""
+        if isinstance(kind, str):
+            kind = {"jacobi": DG_PRECOND_JACOBI, "twolevel": DG_PRECOND_TWOLEVEL}[kind]
+        _check(_lib.dg_grid_set_precond(self.h, int(kind)))
 
     def close(self):
         if getattr(self, "h", None):
