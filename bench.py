@@ -31,6 +31,9 @@ WORKLOADS = {
     "shear512_n4": dict(N=512, n=4, D=1e-4, dt=5e-4, tol=1e-10, field="shear_layer"),
     "sinsin32_n3": dict(N=32, n=3, D=0.0, dt=1e-3, tol=1e-12, field="sin_sin_noise"),
     "random1024_n5": dict(N=1024, n=5, D=0.0, dt=2e-4, tol=1e-10, field="random_phase"),
+    # not single runs: handled by run_batch / run_serve
+    "batch64": dict(N=0, n=0, D=0.0, dt=0.0, tol=1e-10, field="random_phase"),
+    "serve": dict(N=0, n=0, D=0.0, dt=0.0, tol=1e-10, field="mixed"),
 }
 DEFAULT_WORKLOAD = "shear512_n4"
 L2_BYTES = 129 * 1024 * 1024
@@ -125,17 +128,18 @@ def _gpu_index_for_smi(local_rank):
 SAMPLE_CELLS = 128
 
 
-def oracle_sample(wl, cg_sample_iters=4):
+def oracle_sample(wl, cg_sample_iters=4, precond="twolevel"):
     """Times the FP64 oracle on a SAMPLE_CELLS^2 periodic grid of the same n, field and
     parameters: one right-hand side (bracket + viscous term + AB3 update), the Poisson setup
-    and cg_sample_iters CG iterations.  Returns seconds per dof for each part (the oracle's
-    cost is linear in the dof count)."""
+    and cg_sample_iters CG iterations with the given preconditioner.  Returns seconds per dof
+    for each part (the oracle's cost is linear in the dof count, up to the log of its FFT)."""
     import numpy as np
     from oracle.operators import Operators
-    from oracle.solver import pcg, poisson_rhs
+    from oracle.solver import TwoLevel, pcg, poisson_rhs
     from oracle.tables import Grid
     g = Grid(SAMPLE_CELLS, SAMPLE_CELLS, wl["n"])
     ops = Operators(g)
+    M = TwoLevel(ops) if precond == "twolevel" else None
     X, Y = g.mesh()
     w = make_field(wl["field"], X, Y)
     psi = 0.01 * np.sin(X) * np.cos(Y)
@@ -149,15 +153,15 @@ def oracle_sample(wl, cg_sample_iters=4):
     t1 = time.perf_counter()
     b = poisson_rhs(ops, w1)
     t2 = time.perf_counter()
-    pcg(ops, b, psi, 1e-30, cg_sample_iters, fixed_iters=cg_sample_iters)
+    pcg(ops, b, psi, 1e-30, cg_sample_iters, fixed_iters=cg_sample_iters, precond=M)
     t3 = time.perf_counter()
     # pcg includes one setup apply (r0 = b - A x0) besides the iterations
     return {"rhs_s_per_dof": (t1 - t0) / dof, "setup_s_per_dof": (t2 - t1) / dof,
             "cg_s_per_dof_iter": (t3 - t2) / dof / (cg_sample_iters + 1), "sample_dof": dof}
 
 
-def oracle_iters_per_step(name):
-    path = os.path.join(ROOT, "tests", "golden", "cg_iterations_shear512_n4.json")
+def oracle_iters_per_step(name, precond="twolevel"):
+    path = os.path.join(ROOT, "tests", "golden", "cg_iterations_shear512_n4_%s.json" % precond)
     if name == "shear512_n4" and os.path.exists(path):
         d = json.load(open(path))
         if d.get("ab3_iters_mean"):
@@ -165,28 +169,29 @@ def oracle_iters_per_step(name):
     return None, None
 
 
-def cpu_baseline(name, wl, native_iters):
+def cpu_baseline(name, wl, native_iters, precond="twolevel"):
     """Runs the oracle sample single-threaded in a child process; returns the cpu_baseline
     object of the JSON line."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0,%r); import bench; "
-            "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r])))" % (ROOT, name))
+            "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r], 4, %r)))" % (ROOT, name, precond))
     t0 = time.time()
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         return {"value": None, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
                 "sample": "failed: " + out.stderr.strip()[-200:]}
     s = json.loads(out.stdout.strip().splitlines()[-1])
-    k, ksrc = oracle_iters_per_step(name)
+    k, ksrc = oracle_iters_per_step(name, precond)
     if k is None:
         k, ksrc = native_iters, "CG iterations per step measured on the GPU in this run"
     sec_per_dof_step = s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"]
     return {"value": 1e-6 / sec_per_dof_step, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
             "sample": ("FP64 NumPy oracle, single thread, on a %dx%d-cell grid (n=%d, %d dof): one RHS "
                        "(bracket + viscous term + AB3 update), the Poisson setup and 5 CG operator "
-                       "applications, timed per dof and scaled to one step of %.0f CG iterations (%s); "
-                       "%.1f s of CPU" % (SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], k, ksrc,
-                                           time.time() - t0)),
+                       "applications with the %s preconditioner, timed per dof and scaled to one step "
+                       "of %.0f CG iterations (%s); %.1f s of CPU"
+                       % (SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], precond, k, ksrc,
+                          time.time() - t0)),
             "parts_s_per_dof": s}
 
 
@@ -195,15 +200,15 @@ def run_reference(args, wl, name):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    k, ksrc = oracle_iters_per_step(name)
+    k, ksrc = oracle_iters_per_step(name, args.precond)
     if k is None:
-        k, ksrc = 200.0, "assumed 200 CG iterations per step (no measured count for this workload)"
+        k, ksrc = 30.0, "assumed 30 CG iterations per step (no measured count for this workload)"
     for _ in range(args.warmup):
-        oracle_sample(wl, 1)
+        oracle_sample(wl, 1, args.precond)
     t0 = time.perf_counter()
     secs = []
     for _ in range(args.steps):
-        s = oracle_sample(wl, 1)
+        s = oracle_sample(wl, 1, args.precond)
         secs.append(s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"])
     wall = time.perf_counter() - t0
     dof = wl["N"] * wl["N"] * wl["n"] ** 2
@@ -238,15 +243,25 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "twolevel"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64"])
+    ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel"])
+    ap.add_argument("--no-mixed-compare", action="store_true")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-steps-scale", type=float, default=0.02)
+    ap.add_argument("--serve-max-cells", type=int, default=1024)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, args.workload)
+        return
+    if args.workload == "batch64":
+        run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3 (the first two steps are RK4 start-up steps)")
@@ -267,7 +282,7 @@ def main():
     _build.build()
     from paper_1311_7477_gb300 import dg, fields
 
-    precision = dg.DG_FP64 if args.precision == "fp64" else dg.DG_MIXED
+    precision = {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED, "mixed64": dg.DG_MIXED64}[args.precision]
     N, n = wl["N"], wl["n"]
     g = dg.Grid(N, N, n)
     g.set_precond(args.precond)
@@ -334,7 +349,7 @@ def main():
 
     # --- mixed precision: error of one step against the float64 path from the identical state
     err_vs_fp64 = None
-    if precision == dg.DG_MIXED:
+    if precision != dg.DG_FP64:
         st = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
         kk = sim.get_state(*st)
         ref = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=dg.DG_FP64, cg_tol=wl["tol"], cg_maxit=200000)
@@ -354,6 +369,45 @@ def main():
                        "refine_sweeps_last": int(sim.status().refine_sweeps_last)}
         ref.close()
 
+    # --- the same workload in the mixed-precision modes (timed the same way), and their
+    # one-step error against the float64 path from the identical state
+    modes = None
+    if precision == dg.DG_FP64 and not args.no_mixed_compare:
+        modes = {}
+        st = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+        kk = sim.get_state(*st)
+        ref_w, ref_p = torch.empty_like(st[0]), torch.empty_like(st[0])
+        sim.step(1)
+        sim.get(ref_w, ref_p)
+        for mname, mprec in (("mixed64", dg.DG_MIXED64), ("mixed", dg.DG_MIXED)):
+            ms_ = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=mprec, cg_tol=wl["tol"], cg_maxit=200000)
+            ms_.set_state(kk, *st)
+            ms_.step(1)
+            w1, p1 = torch.empty_like(st[0]), torch.empty_like(st[0])
+            ms_.get(w1, p1)
+            torch.cuda.synchronize()
+            err = {"omega_rel_l2": float(torch.linalg.norm(w1 - ref_w) / torch.linalg.norm(ref_w)),
+                   "psi_rel_l2": float(torch.linalg.norm(p1 - ref_p) / torch.linalg.norm(ref_p))}
+            ms_.step(max(args.warmup - 1, 1))
+            i0 = ms_.status().cg_iters_total
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ms_.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms = e0.elapsed_time(e1)
+            info = ms_.status()
+            modes[mname] = {"value": dof * args.steps * world / (mms / 1e3) / 1e6, "unit": "Mdof·steps/s",
+                            "ms_per_step": mms / args.steps,
+                            "inner_cg_iters_per_step": (info.cg_iters_total - i0) / args.steps,
+                            "refine_sweeps_last": int(info.refine_sweeps_last),
+                            "error_vs_fp64_one_step": err,
+                            "what": {"mixed64": "float64 bracket/viscous term/update, float32 inner CG, "
+                                                "float64 refinement residual",
+                                     "mixed": "float32 bracket and inner CG, float64 update and refinement"}[mname]}
+            ms_.close()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -365,9 +419,17 @@ def main():
     cg_ms_per_launch = cnt.cg_ms / max(cnt.cg_launches, 1)
     rhs_ms_per_launch = cnt.rhs_ms / max(cnt.rhs_launches, 1)
     it_per_launch = (info1.cg_iters_total - info0.cg_iters_total) / max(cnt.cg_launches, 1)
-    flops_iter = 4 * (n + 4) + 10      # Ahat apply (rank-one faces) + 5 vector updates/dots, per dof
-    flops_setup = 4 * (n + 4) + 8
+    # algorithmic work per dof and CG iteration: the operator Ahat with rank-one face coupling
+    # (2 directions x (n + 4) FMA), 5 vector updates / dot products; with the two-level
+    # preconditioner also the cell block solve (n^2 FMA), restriction and prolongation (2 FMA)
+    # and the coarse DFT (4 one-dimensional passes of 5 log2(N) flop per cell, per dof / n^2)
+    import math
+    flops_iter = 4 * (n + 4) + 10
     bytes_iter = 8 * 8                 # x, r, p read+write; q write+read (float64)
+    if args.precond == "twolevel":
+        flops_iter += 2 * n * n + 4 + 2 + 4 * 5 * math.log2(N) / (n * n)
+        bytes_iter += 2 * 8            # z written and read
+    flops_setup = 4 * (n + 4) + 8
     bytes_setup = 6 * 8
     cg_flops = dof * (flops_iter * it_per_launch + flops_setup)
     cg_bytes = dof * (bytes_iter * it_per_launch + bytes_setup)
@@ -397,6 +459,7 @@ def main():
                                "the 129 MB L2" % (12 * dof * 8 / 1e6))),
             "cg_iters_per_step": iters, "rhs_ms": rhs_ms_per_launch, "roofline": roof,
             "error_vs_fp64": err_vs_fp64,
+            "precision_modes": modes,
             "gpu_launches": int(cnt.launches), "clocks": clocks,
             "e2e": {"value": dof * ke * world / e2e_s / 1e6, "unit": "Mdof·steps/s",
                     "h2d_bytes_per_step": int(5 * dof * 8 / ke), "d2h_bytes_per_step": int(2 * dof * 8 / ke) + 24,
@@ -404,12 +467,108 @@ def main():
                     "what": "upload of the full stepper state from pinned host memory, %d steps each followed "
                             "by a host read of (V, E, Omega), download of omega and psi" % ke}}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.workload, wl, iters)
+        line["cpu_baseline"] = cpu_baseline(args.workload, wl, iters, args.precond)
     else:
         line["cpu_baseline"] = None
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _prec(dg, name):
+    return {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED, "mixed64": dg.DG_MIXED64}[name]
+
+
+def run_batch(args):
+    """64 uneven simulations (cells per side in {32,64,128,256}, n in {2..5}, D log-uniform in
+    [1e-5, 1e-3], random phase) advanced together by the persistent batched kernel; the group
+    count is autotuned on the first steps (which count as warm-up)."""
+    import torch
+    from paper_1311_7477_gb300 import build as _build
+    _build.build()
+    from paper_1311_7477_gb300 import dg, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prec = dg.DG_MIXED if args.precision == "mixed" else _prec(dg, args.precision)
+    specs = workloads.ensemble_specs()
+    members = []
+    for sp in specs:
+        g = dg.Grid(sp["N"], sp["N"], sp["n"])
+        g.set_precond(args.precond)
+        w0 = torch.from_numpy(workloads.initial_field(dg, g, sp)).cuda()
+        dt = workloads.stable_dt(dg, sp["N"], sp["n"], sp["D"])
+        members.append((g, dg.Sim(g, w0, D=sp["D"], dt=dt, precision=prec, cg_tol=1e-10, cg_maxit=100000)))
+    b = dg.Batch(len(members))
+    for g, s in members:
+        b.admit(s)
+    dof = sum(g.dof for g, _ in members)
+    stream = torch.cuda.current_stream()
+    best = None
+    tune = {}
+    for G in (2, 4, 8, 16, 32):
+        b.set_groups(G)
+        b.step(1)            # plan + capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tune[G] = e0.elapsed_time(e1)
+        if best is None or tune[G] < tune[best]:
+            best = G
+    b.set_groups(best)
+    b.step(max(args.warmup, 1))
+    torch.cuda.synchronize()
+    before = sum(s.status().cg_iters_total for _, s in members)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = b.status()
+    after = sum(s.status().cg_iters_total for _, s in members)
+    line = {"metric": "Mdof·steps/s", "value": dof * args.steps / (ms / 1e3) / 1e6, "unit": "Mdof·steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f32+f64", "mixed64": "f32+f64", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "batch64", "members": len(members), "dof_total": dof,
+                       "cells": "32..256 per side", "n": "2..5", "D": "log-uniform [1e-5, 1e-3]",
+                       "precision": args.precision, "cg_preconditioner": args.precond,
+                       "groups": best, "autotune_ms_per_step": tune, "graph": st["graph"]},
+            "inner_cg_iters_per_member_step": (after - before) / (args.steps * len(members)),
+            "gpu_launches": args.steps}
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """The served workload: Poisson arrivals at 20 requests/s (seed 7), cells per side in
+    {64,...,1024} (powers of two), n in {3,4,5}, D log-uniform, random-phase or shear-layer
+    fields; step counts U{100..2000} scaled by --serve-steps-scale (the unscaled trace is about
+    an hour of GPU work)."""
+    import torch
+    from paper_1311_7477_gb300 import build as _build
+    _build.build()
+    from paper_1311_7477_gb300 import dg, serve, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Ns = tuple(N for N in (64, 128, 256, 512, 1024) if N <= args.serve_max_cells)
+    trace = workloads.request_trace(count=args.serve_requests, Ns=Ns)
+    for r in trace:
+        r["steps"] = max(3, int(round(r["steps"] * args.serve_steps_scale)))
+    prec = dg.DG_MIXED if args.precision == "fp64" else _prec(dg, args.precision)
+    srv = serve.Server(max_active=64, hbm_budget=200e9, precision=prec, precond=args.precond)
+    rep = srv.run(trace)
+    line = {"metric": "Mdof·steps/s", "value": rep["mdof_steps_per_s"], "unit": "Mdof·steps/s", "n_gpus": 1,
+            "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serve", "requests": len(trace), "rate_per_s": 20, "cells": list(Ns),
+                       "n": [3, 4, 5], "steps_scale": args.serve_steps_scale,
+                       "precision": {0: "fp64", 1: "mixed", 2: "mixed64"}[prec], "cg_preconditioner": args.precond},
+            "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
+            "served": rep}
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

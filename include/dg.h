@@ -47,8 +47,9 @@ extern "C" {
 #define DG_PRECOND_TWOLEVEL 1  /* cell block solves + DFT coarse solve on cell averages    */
 
 /* ---- precision modes ------------------------------------------------------------- */
-#define DG_FP64 0   /* everything in float64                                               */
-#define DG_MIXED 1  /* bracket and inner CG in float32, float64 refinement, state and sums */
+#define DG_FP64 0     /* everything in float64                                             */
+#define DG_MIXED 1    /* bracket and inner CG in float32, float64 refinement, state and sums */
+#define DG_MIXED64 2  /* bracket in float64, inner CG in float32, float64 refinement, state  */
 
 typedef struct dg_grid dg_grid;
 typedef struct dg_sim dg_sim;
@@ -257,6 +258,38 @@ typedef struct {
  * the launching stream (read back by dg_sim_get_counters, which synchronises the stream). */
 int dg_sim_set_timing(dg_sim* s, int enable);
 int dg_sim_get_counters(dg_sim* s, dg_sim_counters* c, void* stream);
+
+/* ---- batches: many simulations in one persistent kernel ------------------------------ */
+
+/*
+ * A batch advances many independent simulations (any grids, n, viscosities, precisions) with
+ * ONE cooperative persistent launch per dg_batch_step: the launch's blocks are split into
+ * groups; each group runs whole AB3 steps (the fused bracket / viscous term / update of
+ * Sec. 6 and the Poisson solve) for the simulations queued on it, one after the other, with
+ * its own capped barrier; the groups run concurrently.  The launch is captured once in a
+ * CUDA graph and replayed.  Simulations keep their state in their own buffers: a simulation
+ * can be retired and stepped alone (dg_step) or re-admitted at any time between calls.
+ *
+ * dg_batch_create  -- room for max_sims >= 1 simulations.  Errors: DG_ERR_ARG, DG_ERR_NOMEM.
+ * dg_batch_admit   -- adds s (which must outlive its membership); if s has taken fewer than
+ *                     two steps, its RK4 start-up steps run first, alone (synchronously on the
+ *                     stream).  Errors: DG_ERR_NOMEM when full, DG_ERR_ARG if already admitted.
+ * dg_batch_retire  -- removes s.
+ * dg_batch_set_groups -- number of block groups (0: automatic, at most 8); takes effect at the
+ *                     next step.
+ * dg_batch_step    -- every admitted simulation advances nsteps AB3 steps (asynchronous).
+ * dg_batch_status  -- synchronises; reports whether the graph path is used, the group count
+ *                     and the launches so far; returns the first error of the batch kernel or
+ *                     of any member's solves (DG_ERR_TIMEOUT, DG_ERR_NOCONV, ...).
+ */
+int dg_batch_create(dg_batch** b, int max_sims);
+int dg_batch_destroy(dg_batch* b);
+int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream);
+int dg_batch_retire(dg_batch* b, dg_sim* s);
+int dg_batch_size(const dg_batch* b);
+int dg_batch_set_groups(dg_batch* b, int ngroups);
+int dg_batch_step(dg_batch* b, int nsteps, void* stream);
+int dg_batch_status(dg_batch* b, int* uses_graph, int* ngroups, long long* launches, void* stream);
 
 #ifdef __cplusplus
 }

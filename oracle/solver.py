@@ -136,7 +136,10 @@ def pcg(ops, b, x0, tol, maxit, fixed_iters=0, precond=None):
             converged = False
             break
         q = ops.A(p)
-        alpha = rz / float(np.sum(p * q))
+        pq = float(np.sum(p * q))
+        if pq <= 0.0 and fixed_iters > 0:
+            break          # exact convergence reached before the fixed count (tiny systems)
+        alpha = rz / pq
         x = x + alpha * p
         r = r - alpha * q
         z = M(r)

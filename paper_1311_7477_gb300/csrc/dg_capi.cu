@@ -187,6 +187,8 @@ struct dg_grid {
   Workspace ws;
   int precond = 0;  // DG_PRECOND_JACOBI or DG_PRECOND_TWOLEVEL
   PcTables pc;
+  void* d_opsd = nullptr;  // device copies of the operator tables (batched kernel)
+  void* d_opsf = nullptr;
 };
 
 struct dg_sim {
@@ -461,6 +463,14 @@ int build_pc(dg_grid* g) {
   return DG_OK;
 }
 
+int upload_ops(dg_grid* g) {
+  CUDA_TRY(cudaMalloc(&g->d_opsd, sizeof(g->ops.d)));
+  CUDA_TRY(cudaMemcpy(g->d_opsd, g->ops.d, sizeof(g->ops.d), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(&g->d_opsf, sizeof(g->ops.f)));
+  CUDA_TRY(cudaMemcpy(g->d_opsf, g->ops.f, sizeof(g->ops.f), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
 PrecondArgs<double> pc_args(const dg_grid* g, const Workspace& w) {
   PrecondArgs<double> P{};
   P.Bt = g->pc.Bt;
@@ -688,6 +698,7 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
   int rc = alloc_ws(g->ws, ndof_of(g), co_resident_cap(g), true);
   if (!rc) rc = alloc_ws_precond(g->ws, (size_t)Nx * Ny, false);
   if (!rc) rc = build_pc(g);
+  if (!rc) rc = upload_ops(g);
   if (rc) {
     free_ws(g->ws);
     free_pc(g->pc);
@@ -702,6 +713,8 @@ int dg_grid_destroy(dg_grid* g) {
   if (!g) return DG_OK;
   free_ws(g->ws);
   free_pc(g->pc);
+  cudaFree(g->d_opsd);
+  cudaFree(g->d_opsf);
   delete g;
   return DG_OK;
 }
@@ -737,7 +750,7 @@ int dg_grid_set_tiles(dg_grid* g, int TY, int TX) {
     return DG_OK;
   }
   if (TY < 1 || TX < 1 || TY > 64 || TX > 64) return fail(DG_ERR_ARG, "tile must be 1..64 cells per side");
-  const size_t rs = (size_t)(TY + 2) * (TX + 2) * (7 * g->n * g->n + 12 * g->n) * sizeof(double);
+  const size_t rs = (size_t)(TY + 2) * (TX + 2) * (7 * (g->n * g->n + 1) + 12 * g->n) * sizeof(double);
   if (rs > 200 * 1024) return fail(DG_ERR_ARG, "tile %dx%d needs %zu B of shared memory", TY, TX, rs);
   g->rTY = g->cTY = TY;
   g->rTX = g->cTX = TX;
@@ -839,7 +852,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
               cudaStream_t st) {
   dg_grid* g = s->g;
   int rc;
-  if (s->precision == DG_MIXED) {
+  if (s->precision != DG_FP64) {
     MixedArgs A{};
     A.omega = omega;
     A.xa = xa;
@@ -1019,7 +1032,8 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
   if (!aligned8(omega0)) return fail(DG_ERR_ARG, "misaligned pointer");
   if (!(D >= 0.0) || !(dt > 0.0) || !(cg_tol > 0.0) || cg_maxit < 1)
     return fail(DG_ERR_ARG, "need D >= 0, dt > 0, cg_tol > 0, cg_maxit >= 1");
-  if (precision != DG_FP64 && precision != DG_MIXED) return fail(DG_ERR_ARG, "unknown precision %d", precision);
+  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED64)
+    return fail(DG_ERR_ARG, "unknown precision %d", precision);
   cudaStream_t st = as_stream(stream);
   dg_sim* s = new (std::nothrow) dg_sim();
   if (!s) return fail(DG_ERR_NOMEM, "host allocation failed");
@@ -1048,8 +1062,8 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
     CUDA_TRY(cudaMalloc(&s->k2, rbytes));
     CUDA_TRY(cudaMalloc(&s->k3, rbytes));
     if (int rc = alloc_ws(s->ws, ndof_of(g), co_resident_cap(g), false)) return rc;
-    if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision == DG_MIXED)) return rc;
-    return precision == DG_MIXED ? alloc_ws_mixed(s->ws) : DG_OK;
+    if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision != DG_FP64)) return rc;
+    return precision != DG_FP64 ? alloc_ws_mixed(s->ws) : DG_OK;
   };
   int rc = alloc_all();
   if (!rc) rc = (cudaMemcpyAsync(s->omega[0], omega0, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess)
@@ -1345,3 +1359,336 @@ extern "C" int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double 
   if (relres) *relres = s.last_rhob > 0 ? std::sqrt(std::max(s.last_rho, 0.0) / s.last_rhob) : 0.0;
   return flags_to_status(s.last_flags);
 }
+
+// ---------------------------------------------------------------------------------------
+// Batches: many simulations advanced by one persistent kernel (batch_kernel)
+// ---------------------------------------------------------------------------------------
+struct dg_batch {
+  int max_sims = 0;
+  std::vector<dg_sim*> sims;
+  int ngroups_req = 0;  // 0: automatic
+  bool dirty = true;    // composition or plan changed: re-plan, re-upload, re-capture
+  BatchSim* d_sims = nullptr;
+  int* d_order = nullptr;
+  BatchGroup* d_groups = nullptr;
+  SyncState* d_sync = nullptr;
+  int* d_error = nullptr;
+  int cap_groups = 256;
+  int grid = 0, ngroups = 0;
+  size_t smem = 0;
+  std::vector<int> order;
+  std::vector<BatchGroup> groups;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  bool use_graph = true;
+  char graph_error[256] = "";
+  long long launches = 0;
+};
+
+namespace {
+
+BatchSim make_batch_sim(dg_sim* s) {
+  dg_grid* g = s->g;
+  BatchSim b{};
+  b.n = g->n;
+  b.precision = s->precision == DG_FP64 ? 0 : (s->precision == DG_MIXED ? 1 : 2);
+  b.precond = g->precond;
+  b.Gr = geom_of(g, g->rTY, g->rTX);
+  b.Gc = geom_of(g, g->cTY, g->cTX);
+  b.ops_d = g->d_opsd;
+  b.ops_f = g->d_opsf;
+  for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
+  for (int i = 0; i < 3; ++i) {
+    b.psi[i] = s->psi[i];
+    b.R[i] = s->R[i];
+  }
+  b.oc = s->oc;
+  b.p0 = s->p0;
+  b.p1 = s->p1;
+  b.p2 = s->p2;
+  b.r1 = s->r1;
+  b.r2 = s->r2;
+  b.rfree = s->rfree;
+  b.step = s->step;
+  b.D = s->D;
+  b.dt = s->dt;
+  b.tol2 = s->tol * s->tol;
+  b.tol_in2 = s->tol_in * s->tol_in;
+  b.maxit = s->maxit;
+  b.max_sweeps = s->max_sweeps;
+  b.fixed_iters = s->fixed_iters;
+  b.sumW = g->Lx * g->Ly;
+  b.r = s->ws.r;
+  b.p0v = s->ws.p0;
+  b.p1v = s->ws.p1;
+  b.q = s->ws.q;
+  b.part = s->ws.part;
+  b.rf = s->ws.rf;
+  b.fr = s->ws.fr;
+  b.fe = s->ws.fe;
+  b.fp0 = s->ws.fp0;
+  b.fp1 = s->ws.fp1;
+  b.fq = s->ws.fq;
+  b.partf = s->ws.partf;
+  b.status = s->ws.status;
+  b.pc = pc_args(g, s->ws);
+  b.pcf = pc_args_f(g, s->ws);
+  return b;
+}
+
+// Dynamic shared memory one simulation needs in batch_kernel (RHS tile and solve share it).
+size_t batch_smem_for(const dg_sim* s) {
+  const dg_grid* g = s->g;
+  const Geom Gr = geom_of(g, g->rTY, g->rTX), Gc = geom_of(g, g->cTY, g->cTX);
+  const int Lmax = std::max(g->Nx, g->Ny);
+  const bool pc = g->precond == DG_PRECOND_TWOLEVEL;
+  size_t out = 0;
+  dispatch_n(g->n, [&](auto nc) {
+    constexpr int N = decltype(nc)::value;
+    const size_t rhs = s->precision == DG_MIXED ? rhs_smem_values<float, N>(Gr.TY, Gr.TX) * sizeof(float)
+                                                : rhs_smem_values<double, N>(Gr.TY, Gr.TX) * sizeof(double);
+    const size_t sol = s->precision == DG_FP64 ? cg_smem_bytes<double, N>(Gc.TY, Gc.TX, Lmax, pc)
+                                               : mixed_smem_bytes<N>(Gc.TY, Gc.TX, Lmax, pc);
+    out = std::max(rhs, sol);
+    return DG_OK;
+  });
+  return out;
+}
+
+// Splits the simulations into groups of balanced work (longest processing time first; work
+// ~ dof) and the co-resident blocks among the groups in proportion to their work.
+int batch_plan(dg_batch* b, int dev_sms) {
+  const int ns = (int)b->sims.size();
+  size_t smem = 0;
+  for (dg_sim* s : b->sims) smem = std::max(smem, batch_smem_for(s));
+  int optin = 0;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin) return fail(DG_ERR_ARG, "batch needs %zu B of shared memory per block (max %d)", smem, optin);
+  if (int rc = set_smem(batch_kernel, smem)) return rc;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, smem));
+  if (per_sm < 1) return fail(DG_ERR_CUDA, "batch kernel does not fit on an SM");
+  int grid = per_sm * dev_sms;
+  for (dg_sim* s : b->sims) grid = std::min(grid, s->ws.grid_cap);
+  int G = b->ngroups_req > 0 ? b->ngroups_req : std::min(ns, 8);
+  G = std::max(1, std::min({G, ns, grid, b->cap_groups}));
+  std::vector<int> idx(ns);
+  for (int i = 0; i < ns; ++i) idx[i] = i;
+  auto work = [&](int i) { return (double)ndof_of(b->sims[i]->g); };
+  std::sort(idx.begin(), idx.end(), [&](int a, int c) { return work(a) > work(c); });
+  std::vector<double> gw(G, 0.0);
+  std::vector<std::vector<int>> members(G);
+  for (int i : idx) {
+    const int k = int(std::min_element(gw.begin(), gw.end()) - gw.begin());
+    gw[k] += work(i);
+    members[k].push_back(i);
+  }
+  double total = 0.0;
+  for (double w : gw) total += w;
+  std::vector<int> nb(G, 1);
+  int left = grid - G;
+  for (int k = 0; k < G && left > 0; ++k) {
+    const int extra = std::min(left, int(std::floor((grid - G) * gw[k] / total)));
+    nb[k] += extra;
+    left -= extra;
+  }
+  for (int k = 0; left > 0; k = (k + 1) % G, --left) nb[k] += 1;
+  b->order.clear();
+  b->groups.assign(G, BatchGroup{});
+  int fb = 0;
+  for (int k = 0; k < G; ++k) {
+    b->groups[k].first_block = fb;
+    b->groups[k].nblocks = nb[k];
+    b->groups[k].first = (int)b->order.size();
+    b->groups[k].count = (int)members[k].size();
+    b->groups[k].sync = b->d_sync + k;
+    for (int i : members[k]) b->order.push_back(i);
+    fb += nb[k];
+  }
+  std::vector<BatchSim> hs(ns);
+  for (int i = 0; i < ns; ++i) hs[i] = make_batch_sim(b->sims[i]);
+  CUDA_TRY(cudaMemcpy(b->d_sims, hs.data(), ns * sizeof(BatchSim), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_order, b->order.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_groups, b->groups.data(), G * sizeof(BatchGroup), cudaMemcpyHostToDevice));
+  b->grid = grid;
+  b->ngroups = G;
+  b->smem = smem;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->dirty = false;
+  return DG_OK;
+}
+
+int batch_enqueue(dg_batch* b, int nsteps, cudaStream_t st) {
+  CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, b->ngroups * sizeof(SyncState), st));
+  BatchArgs A{b->d_sims, b->d_order, b->d_groups, b->ngroups, nsteps, b->d_error};
+  // cudaLaunchKernelEx with the cooperative attribute: the form of a cooperative launch
+  // that stream capture (and so the CUDA graph) accepts.
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = b->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUDA_TRY(cudaLaunchKernelEx(&cfg, batch_kernel, A));
+  return DG_OK;
+}
+
+// Host mirror of the rotations the kernel applies to every simulation per step.
+void batch_advance_host(dg_batch* b, int nsteps) {
+  for (dg_sim* s : b->sims)
+    for (int k = 0; k < nsteps; ++k) {
+      s->oc ^= 1;
+      const int p0 = s->p0, p1 = s->p1, p2 = s->p2;
+      s->p0 = p2;
+      s->p1 = p0;
+      s->p2 = p1;
+      const int r1 = s->r1, r2 = s->r2, rf = s->rfree;
+      s->r1 = rf;
+      s->r2 = r1;
+      s->rfree = r2;
+      s->step += 1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_batch_create(dg_batch** bp, int max_sims) {
+  if (!bp || max_sims < 1) return fail(DG_ERR_ARG, "bad arguments");
+  *bp = nullptr;
+  dg_batch* b = new (std::nothrow) dg_batch();
+  if (!b) return fail(DG_ERR_NOMEM, "host allocation failed");
+  b->max_sims = max_sims;
+  auto alloc = [&]() -> int {
+    CUDA_TRY(cudaMalloc(&b->d_sims, max_sims * sizeof(BatchSim)));
+    CUDA_TRY(cudaMalloc(&b->d_order, max_sims * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&b->d_groups, b->cap_groups * sizeof(BatchGroup)));
+    CUDA_TRY(cudaMalloc(&b->d_sync, b->cap_groups * sizeof(SyncState)));
+    CUDA_TRY(cudaMalloc(&b->d_error, sizeof(int)));
+    CUDA_TRY(cudaMemset(b->d_error, 0, sizeof(int)));
+    return DG_OK;
+  };
+  if (int rc = alloc()) {
+    dg_batch_destroy(b);
+    return rc;
+  }
+  *bp = b;
+  return DG_OK;
+}
+
+int dg_batch_destroy(dg_batch* b) {
+  if (!b) return DG_OK;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->d_sims);
+  cudaFree(b->d_order);
+  cudaFree(b->d_groups);
+  cudaFree(b->d_sync);
+  cudaFree(b->d_error);
+  delete b;
+  return DG_OK;
+}
+
+int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream) {
+  if (!b || !s) return fail(DG_ERR_ARG, "NULL argument");
+  if ((int)b->sims.size() >= b->max_sims) return fail(DG_ERR_NOMEM, "batch is full (%d simulations)", b->max_sims);
+  for (dg_sim* t : b->sims)
+    if (t == s) return fail(DG_ERR_ARG, "simulation already in the batch");
+  if (s->step < 2)
+    if (int rc = dg_step(s, int(2 - s->step), stream)) return rc;  // RK4 start-up steps on their own
+  b->sims.push_back(s);
+  b->dirty = true;
+  return DG_OK;
+}
+
+int dg_batch_retire(dg_batch* b, dg_sim* s) {
+  if (!b || !s) return fail(DG_ERR_ARG, "NULL argument");
+  for (size_t i = 0; i < b->sims.size(); ++i)
+    if (b->sims[i] == s) {
+      b->sims.erase(b->sims.begin() + i);
+      b->dirty = true;
+      return DG_OK;
+    }
+  return fail(DG_ERR_ARG, "simulation not in the batch");
+}
+
+int dg_batch_size(const dg_batch* b) { return b ? (int)b->sims.size() : 0; }
+
+int dg_batch_set_groups(dg_batch* b, int ngroups) {
+  if (!b || ngroups < 0) return fail(DG_ERR_ARG, "bad arguments");
+  b->ngroups_req = ngroups;
+  b->dirty = true;
+  return DG_OK;
+}
+
+int dg_batch_step(dg_batch* b, int nsteps, void* stream) {
+  if (!b || nsteps < 0) return fail(DG_ERR_ARG, "bad arguments");
+  if (b->sims.empty() || nsteps == 0) return DG_OK;
+  cudaStream_t st = as_stream(stream);
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (b->dirty)
+    if (int rc = batch_plan(b, sms)) return rc;
+  if (b->use_graph && (!b->graph || b->graph_steps != nsteps)) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc_enq = (e == cudaSuccess) ? batch_enqueue(b, nsteps, cs) : DG_ERR_CUDA;
+    const cudaError_t e_end = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess && rc_enq == DG_OK && graph) e = cudaGraphInstantiate(&b->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (e != cudaSuccess || rc_enq != DG_OK || !b->graph) {
+      snprintf(b->graph_error, sizeof(b->graph_error), "%s", e != cudaSuccess ? cudaGetErrorString(e) : g_err);
+      b->graph = nullptr;
+      b->use_graph = false;  // fall back to direct cooperative launches
+    } else {
+      b->graph_steps = nsteps;
+    }
+  }
+  if (b->graph) {
+    CUDA_TRY(cudaGraphLaunch(b->graph, st));
+  } else if (int rc = batch_enqueue(b, nsteps, st)) {
+    return rc;
+  }
+  b->launches += 1;
+  batch_advance_host(b, nsteps);
+  return DG_OK;
+}
+
+int dg_batch_status(dg_batch* b, int* uses_graph, int* ngroups, long long* launches, void* stream) {
+  if (!b) return fail(DG_ERR_ARG, "NULL argument");
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, b->d_error, sizeof(int), cudaMemcpyDeviceToHost, as_stream(stream)));
+  CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+  if (uses_graph) *uses_graph = b->graph ? 1 : 0;
+  if (!b->graph && b->graph_error[0]) snprintf(g_err, sizeof(g_err), "graph capture unavailable: %s", b->graph_error);
+  if (ngroups) *ngroups = b->ngroups;
+  if (launches) *launches = b->launches;
+  if (err) return fail(DG_ERR_TIMEOUT, "a device-side wait of the batched kernel hit its cap");
+  for (dg_sim* s : b->sims) {
+    SolveStatus ss;
+    if (int rc = read_status(s->ws, &ss, as_stream(stream))) return rc;
+    if (ss.flags) return flags_to_status(ss.flags);
+  }
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -41,6 +41,9 @@ struct Geom {
 
 // One tile of cells and its one-cell halo ring in shared memory: box cell (br, bc) holds
 // grid cell (ty0 + br - 1, tx0 + bc - 1) (periodic wrap); the box row stride is BW = TX + 2.
+// A staged cell occupies N*N + 1 values (one pad value: with a stride of N*N, a multiple of
+// the 32 banks for most N, the lanes of a warp reading the same node of different cells or
+// lines would hit the same bank).
 struct TileBox {
   int ty0, tx0, TYe, TXe, BW;
 };
@@ -77,7 +80,7 @@ __device__ __forceinline__ void stage_box(const Geom& G, const TileBox& B, T* sU
       if (rowhalo && colhalo && !corners) continue;
       const int cx = wrap_index(B.tx0 + bc - 1, G.Nx);
       const size_t g = (rowbase + cx) * NN + k;
-      sU[(br * B.BW + bc) * NN + k] = load(g, k, !(rowhalo || colhalo));
+      sU[(br * B.BW + bc) * (NN + 1) + k] = load(g, k, !(rowhalo || colhalo));
     }
   }
 }
@@ -102,7 +105,7 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
       const int c = i / N, line = i - (i / N) * N;
       const int ry = c / wx + y0, rx = c - (c / wx) * wx - 1;
       const int lc = (ry + 1) * B.BW + rx + 1;
-      const T* u = sUx + lc * NN + line * N;
+      const T* u = sUx + lc * (NN + 1) + line * N;
       T tr = T(0), tl = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
@@ -116,7 +119,7 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
       const int c = ii / N, line = ii - (ii / N) * N;
       const int ry = c / wy - 1, rx = c - (c / wy) * wy + x0;
       const int lc = (ry + 1) * B.BW + rx + 1;
-      const T* u = sUy + lc * NN + line;
+      const T* u = sUy + lc * (NN + 1) + line;
       T tr = T(0), tl = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
@@ -133,7 +136,7 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
 template <typename T, int N>
 __device__ __forceinline__ T op_x_at(const T* sU, const T* tXR, const T* tXL, const Op1D<T, N>& o,
                                      int lc, int a, int b) {
-  const T* u = sU + lc * (N * N) + a * N;
+  const T* u = sU + lc * (N * N + 1) + a * N;
   T acc = o.a[b] * tXR[(lc + 1) * N + a];
   acc = fma(o.d[b], tXL[(lc - 1) * N + a], acc);
 #pragma unroll
@@ -145,7 +148,7 @@ __device__ __forceinline__ T op_x_at(const T* sU, const T* tXR, const T* tXL, co
 template <typename T, int N>
 __device__ __forceinline__ T op_y_at(const T* sU, const T* tYR, const T* tYL, const Op1D<T, N>& o,
                                      int lc, int BW, int a, int b) {
-  const T* u = sU + lc * (N * N) + b;
+  const T* u = sU + lc * (N * N + 1) + b;
   T acc = o.a[a] * tYR[(lc + BW) * N + b];
   acc = fma(o.d[a], tYL[(lc - BW) * N + b], acc);
 #pragma unroll
@@ -207,8 +210,9 @@ struct SyncState {
 // below) and raise kFlagTimeout; every later barrier then returns false at once.
 constexpr unsigned long long kSpinCap = 1ull << 23;
 
-// All blocks of a cooperative launch meet here.  Returns false if any block raised an error.
-__device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag) {
+// The nblk blocks of a (virtual) grid meet here: all blocks of a cooperative launch, or the
+// blocks of one group of a batched launch.  Returns false if any block raised an error.
+__device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag, unsigned int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &s->gen;
@@ -216,7 +220,7 @@ __device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag) {
     const unsigned int gen0 = *vgen;
     __threadfence();
     const unsigned int arrived = atomicAdd(&s->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == nblk) {
       atomicExch(&s->count, 0u);
       __threadfence();
       atomicAdd(&s->gen, 1u);
@@ -228,7 +232,7 @@ __device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag) {
           atomicCAS(&s->error, 0, kFlagTimeout);
           break;
         }
-        __nanosleep(100);
+        if (spins > 4096) __nanosleep(100);  // poll tightly first: most waits are short
       }
     }
     __threadfence();

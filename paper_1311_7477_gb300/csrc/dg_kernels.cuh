@@ -53,25 +53,26 @@ struct RhsArgs {
 
 template <typename T, int N>
 __host__ __device__ constexpr size_t rhs_smem_values(int TY, int TX) {
-  return (size_t)(TY + 2) * (TX + 2) * (7 * N * N + 12 * N);
+  return (size_t)(TY + 2) * (TX + 2) * (7 * (N * N + 1) + 12 * N);
 }
 
+// One tile of the right-hand side (smem: rhs_smem_values<T, N>(G.TY, G.TX) values of T).
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
-                                                      const __grid_constant__ RhsArgs<T> A) {
+__device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, const RhsArgs<T>& A, int tile,
+                                         unsigned char* smem_raw) {
   constexpr int NN = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CS = NN + 1;  // padded cell stride in shared memory
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const TileBox B = make_box(G, blockIdx.x);
+  const TileBox B = make_box(G, tile);
   const int boxc = (G.TY + 2) * (G.TX + 2);
   T* sPsi = sm;
-  T* sOm = sPsi + boxc * NN;
-  T* sFx = sOm + boxc * NN;  // f_x, later h2 = f_x g - f g_x   (cells with rx in [0,TXe))
-  T* sGx = sFx + boxc * NN;
-  T* sFy = sGx + boxc * NN;  // f_y, later h1 = f g_y - f_y g   (cells with ry in [0,TYe))
-  T* sGy = sFy + boxc * NN;
-  T* sJ = sGy + boxc * NN;   // J++ on the tile
-  T* t0 = sJ + boxc * NN;
+  T* sOm = sPsi + boxc * CS;
+  T* sFx = sOm + boxc * CS;  // f_x, later h2 = f_x g - f g_x   (cells with rx in [0,TXe))
+  T* sGx = sFx + boxc * CS;
+  T* sFy = sGx + boxc * CS;  // f_y, later h1 = f g_y - f_y g   (cells with ry in [0,TYe))
+  T* sGy = sFy + boxc * CS;
+  T* sJ = sGy + boxc * CS;   // J++ on the tile
+  T* t0 = sJ + boxc * CS;
   T *tPxR = t0, *tPxL = t0 + boxc * N, *tPyR = t0 + 2 * boxc * N, *tPyL = t0 + 3 * boxc * N;
   T *tOxR = t0 + 4 * boxc * N, *tOxL = t0 + 5 * boxc * N, *tOyR = t0 + 6 * boxc * N, *tOyL = t0 + 7 * boxc * N;
   T *tLxR = t0 + 8 * boxc * N, *tLxL = t0 + 9 * boxc * N, *tLyR = t0 + 10 * boxc * N, *tLyL = t0 + 11 * boxc * N;
@@ -101,8 +102,8 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
         const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
         const int lc = (ry + 1) * BW + rx + 1;
         const int a = k / N, b = k - (k / N) * N;
-        sFx[lc * NN + k] = op_x_at<T, N>(sPsi, tPxR, tPxL, C.dx, lc, a, b);
-        sGx[lc * NN + k] = op_x_at<T, N>(sOm, tOxR, tOxL, C.dx, lc, a, b);
+        sFx[lc * CS + k] = op_x_at<T, N>(sPsi, tPxR, tPxL, C.dx, lc, a, b);
+        sGx[lc * CS + k] = op_x_at<T, N>(sOm, tOxR, tOxL, C.dx, lc, a, b);
       } else {
         const int ii = i - n1;
         const int c = ii / NN, k = ii - (ii / NN) * NN;
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
         const int ry = c / w, rx = c - (c / w) * w - 1;
         const int lc = (ry + 1) * BW + rx + 1;
         const int a = k / N, b = k - (k / N) * N;
-        sFy[lc * NN + k] = op_y_at<T, N>(sPsi, tPyR, tPyL, C.dy, lc, BW, a, b);
-        sGy[lc * NN + k] = op_y_at<T, N>(sOm, tOyR, tOyL, C.dy, lc, BW, a, b);
+        sFy[lc * CS + k] = op_y_at<T, N>(sPsi, tPyR, tPyL, C.dy, lc, BW, a, b);
+        sGy[lc * CS + k] = op_y_at<T, N>(sOm, tOyR, tOyL, C.dy, lc, BW, a, b);
       }
     }
   }
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+    const int o = ((ry + 1) * BW + rx + 1) * CS + k;
     sJ[o] = prod_diff(sFx[o], sGy[o], sFy[o], sGx[o]);
   }
   __syncthreads();
@@ -136,13 +137,13 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
         const int c = i / NN, k = i - (i / NN) * NN;
         const int w = B.TXe + 2;
         const int ry = c / w, rx = c - (c / w) * w - 1;
-        const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+        const int o = ((ry + 1) * BW + rx + 1) * CS + k;
         sFy[o] = prod_diff(sPsi[o], sGy[o], sFy[o], sOm[o]);
       } else {
         const int ii = i - n1;
         const int c = ii / NN, k = ii - (ii / NN) * NN;
         const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
-        const int o = ((ry + 1) * BW + rx + 1) * NN + k;
+        const int o = ((ry + 1) * BW + rx + 1) * CS + k;
         sFx[o] = prod_diff(sFx[o], sOm[o], sPsi[o], sGx[o]);
       }
     }
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
     const int a = k / N, b = k - (k / N) * N;
     const T dxh1 = op_x_at<T, N>(sFy, tPxR, tPxL, C.dx, lc, a, b);
     const T dyh2 = op_y_at<T, N>(sFx, tPyR, tPyL, C.dy, lc, BW, a, b);
-    const T J = ((sJ[lc * NN + k] + dxh1) + dyh2) * third;
+    const T J = ((sJ[lc * CS + k] + dxh1) + dyh2) * third;
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
     if (A.bracket_only) {
       A.omega_out[g] = double(J);
@@ -178,6 +179,14 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
     if (A.R_out) A.R_out[g] = R;
     A.omega_out[g] = fma(A.dt, incr, A.omega_base[g]);
   }
+  __syncthreads();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+                                                      const __grid_constant__ RhsArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rhs_tile<T, N>(C, G, A, blockIdx.x, smem_raw);
 }
 
 // =========================================================================================
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ O
 // =========================================================================================
 template <typename T, int N>
 __host__ __device__ constexpr size_t apply_smem_values(int TY, int TX) {
-  return (size_t)(TY + 2) * (TX + 2) * (N * N + 4 * N);
+  return (size_t)(TY + 2) * (TX + 2) * (N * N + 1 + 4 * N);
 }
 
 template <typename T, int N>
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);
   const int boxc = (G.TY + 2) * (G.TX + 2);
-  T *tXR = sU + boxc * NN, *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
+  T *tXR = sU + boxc * (NN + 1), *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
   const TileBox B = make_box(G, blockIdx.x);
   const Op1D<T, N>& ox = mode == 0 ? C.kx : C.lx;
   const Op1D<T, N>& oy = mode == 0 ? C.ky : C.ly;
@@ -294,33 +303,34 @@ struct SolveCtx {
   T* bcast;
   int* s_flag;
   SyncState* sync;
-  T* part;                        // 4 * gridDim.x: two alternating halves
+  T* part;                        // 4 * vsize: two alternating halves
   int phase;
+  int vrank, vsize;               // this block's rank and the block count of the (virtual) grid
 };
 
 // Block partials of one or two sums -> grid barrier -> the sums in every block (fixed order).
 template <typename T>
 __device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
-  T* ph = X.part + (X.phase & 1) * 2 * gridDim.x;
+  T* ph = X.part + (X.phase & 1) * 2 * X.vsize;
   ++X.phase;
   v0 = block_sum(v0, X.red);
-  if (threadIdx.x == 0) __stcg(ph + blockIdx.x, v0);
-  if (!grid_barrier(X.sync, X.s_flag)) return false;
-  out0 = sum_partials(ph, gridDim.x, 1, X.bcast);
+  if (threadIdx.x == 0) __stcg(ph + X.vrank, v0);
+  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  out0 = sum_partials(ph, X.vsize, 1, X.bcast);
   return true;
 }
 
 template <typename T>
 __device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0, T& out1) {
-  T* ph = X.part + (X.phase & 1) * 2 * gridDim.x;
+  T* ph = X.part + (X.phase & 1) * 2 * X.vsize;
   ++X.phase;
   v0 = block_sum(v0, X.red);
-  if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x, v0);
+  if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank, v0);
   v1 = block_sum(v1, X.red);
-  if (threadIdx.x == 0) __stcg(ph + 2 * blockIdx.x + 1, v1);
-  if (!grid_barrier(X.sync, X.s_flag)) return false;
-  out0 = sum_partials(ph, gridDim.x, 2, X.bcast);
-  out1 = sum_partials(ph + 1, gridDim.x, 2, X.bcast);
+  if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank + 1, v1);
+  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  out0 = sum_partials(ph, X.vsize, 2, X.bcast);
+  out1 = sum_partials(ph + 1, X.vsize, 2, X.bcast);
   return true;
 }
 
@@ -344,7 +354,7 @@ __device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& 
     const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
                 op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-    out(g, k, X.sU[lc * NN + k], q);
+    out(g, k, X.sU[lc * (NN + 1) + k], q);
   }
   __syncthreads();
 }
@@ -360,10 +370,10 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * NN;
+    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
     T zj = T(0);
 #pragma unroll
-    for (int j = 0; j < NN; ++j) zj = fma(X.Bs[k * NN + j], u[j], zj);
+    for (int j = 0; j < NN; ++j) zj = fma(X.Bs[j * NN + k], u[j], zj);  // Bt is symmetric
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
     __stcg(P.z + g, zj);
     rz = fma(u[k], zj, rz);
@@ -371,7 +381,7 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
   const int ncell = B.TYe * B.TXe;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * NN;
+    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
     T v = T(0);
 #pragma unroll
     for (int k = 0; k < NN; ++k) v = fma(C.sw[k], u[k], v);
@@ -400,16 +410,16 @@ __device__ __forceinline__ void st_cplx(Cplx<T>* p, Cplx<T> v) {
 template <typename T>
 __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P, SolveCtx<T>& X, T& ucrc) {
   const int Nx = G.Nx, Ny = G.Ny;
-  for (int row = blockIdx.x; row < Ny; row += gridDim.x) {
+  for (int row = X.vrank; row < Ny; row += X.vsize) {
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
     __syncthreads();
     dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, false);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) st_cplx(&P.C[(size_t)row * Nx + j], X.line0[j]);
     __syncthreads();
   }
-  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
   const T scale = T(1) / (T(Nx) * T(Ny));
-  for (int col = blockIdx.x; col < Nx; col += gridDim.x) {
+  for (int col = X.vrank; col < Nx; col += X.vsize) {
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) X.line0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * Nx + col]);
     __syncthreads();
     dft_line(X.line0, X.line1, Ny, P.log2y, P.twy, false);
@@ -423,9 +433,9 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * Nx + col], X.line1[j]);
     __syncthreads();
   }
-  if (!grid_barrier(X.sync, X.s_flag)) return false;
+  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
   T acc = T(0);
-  for (int row = blockIdx.x; row < Ny; row += gridDim.x) {
+  for (int row = X.vrank; row < Ny; row += X.vsize) {
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
     __syncthreads();
     dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, true);
@@ -447,14 +457,14 @@ __device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, co
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
   T rzb = T(0);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = X.vrank; t < ntiles; t += X.vsize) {
     const TileBox B = make_box(G, t);
     const int nin = B.TYe * B.TXe * NN;
     for (int i = threadIdx.x; i < nin; i += blockDim.x) {
       const int c = i / NN, k = i - (i / NN) * NN;
       const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
       const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-      X.sU[((ry + 1) * B.BW + rx + 1) * NN + k] = __ldcg(r + g);
+      X.sU[((ry + 1) * B.BW + rx + 1) * (NN + 1) + k] = __ldcg(r + g);
     }
     __syncthreads();
     rzb += pc_cells<T, N>(C, G, B, P, X);
@@ -481,7 +491,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t stride = (size_t)X.vsize * blockDim.x;
   int it = 0, restarts = 0;
   T beta = T(0);
   int cur = 0;
@@ -494,7 +504,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       if (max_restarts == 0) break;  // loose inner solves: the recursive residual suffices
       // Verify on the true residual r = b - Ahat y.
       T rt = T(0);
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int t = X.vrank; t < ntiles; t += X.vsize) {
         cg_tile_apply<T, N>(
             C, G, t, X, [&](size_t g, int, bool) { return __ldcg(V.y + g); },
             [&](size_t g, int k, T, T qv) {
@@ -535,7 +545,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
     T* pout = cur ? V.p0 : V.p1;
     // Phase A: p = z + beta p_old (halo recomputed locally), q = Ahat p, p.q.
     T pq = T(0);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = X.vrank; t < ntiles; t += X.vsize) {
       cg_tile_apply<T, N>(
           C, G, t, X,
           [&](size_t g, int k, bool interior) {
@@ -555,14 +565,17 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       return it;
     }
     if (!(pqs > T(0))) {
-      flags |= kFlagBreakdown;
+      // In parity mode (a fixed iteration count) CG may run past exact convergence on tiny
+      // systems, where p.q is rounding noise (zero or negative): stop there.  Anything else
+      // (a non-positive p.q in a tolerance-stopped solve, or NaN) is a breakdown.
+      if (!(fixed_iters > 0 && pqs <= T(0))) flags |= kFlagBreakdown;
       break;
     }
     const T alpha = rz / pqs;
     // Phase B: y += alpha p, r -= alpha q, r.r (and the cell part of the preconditioner).
     T rrb = T(0), rzb = T(0);
     if (!P) {
-      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) {
+      for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) {
         const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
         const T yv = fma(alpha, pv, __ldcg(V.y + i));
         const T rv = fma(-alpha, qv, __ldcg(V.r + i));
@@ -571,7 +584,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
         rrb = fma(rv, rv, rrb);
       }
     } else {
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int t = X.vrank; t < ntiles; t += X.vsize) {
         const TileBox B = make_box(G, t);
         const int nin = B.TYe * B.TXe * NN;
         for (int i = threadIdx.x; i < nin; i += blockDim.x) {
@@ -584,7 +597,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
           __stcg(V.y + g, yv);
           __stcg(V.r + g, rv);
           rrb = fma(rv, rv, rrb);
-          X.sU[((ry + 1) * B.BW + rx + 1) * NN + k] = rv;
+          X.sU[((ry + 1) * B.BW + rx + 1) * (NN + 1) + k] = rv;
         }
         __syncthreads();
         rzb += pc_cells<T, N>(C, G, B, *P, X);
@@ -622,16 +635,16 @@ __device__ __forceinline__ bool project_mean(const Ops2D<T, N>& C, const Geom& G
                                              SolveCtx<T>& X) {
   constexpr int NN = N * N;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t stride = (size_t)X.vsize * blockDim.x;
   T s = T(0);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+  for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
     s = fma(C.sw[i % NN], __ldcg(y + i), s);
   T m = T(0);
   if (!reduce_all(X, s, m)) return false;
   m = m / T(sumW);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+  for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
     __stcg(y + i, fma(-m, C.sw[i % NN], __ldcg(y + i)));
-  return grid_barrier(X.sync, X.s_flag);
+  return grid_barrier(X.sync, X.s_flag, X.vsize);
 }
 
 template <typename T>
@@ -660,7 +673,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 
 template <typename T, int N>
 __host__ __device__ constexpr size_t cg_tile_values(int TY, int TX) {
-  return (size_t)(TY + 2) * (TX + 2) * (N * N + 4 * N);
+  return (size_t)(TY + 2) * (TX + 2) * (N * N + 1 + 4 * N);
 }
 
 template <typename T, int N>
@@ -687,7 +700,7 @@ __device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, co
   }
   const int boxc = (G.TY + 2) * (G.TX + 2);
   X.sU = reinterpret_cast<T*>(p);
-  X.tXR = X.sU + boxc * NN;
+  X.tXR = X.sU + boxc * (NN + 1);
   X.tXL = X.tXR + boxc * N;
   X.tYR = X.tXL + boxc * N;
   X.tYL = X.tYR + boxc * N;
@@ -696,26 +709,17 @@ __device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, co
   __syncthreads();
 }
 
+// The whole Poisson solve on the (virtual) grid of X (context laid out by init_ctx).
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
-                                                     const __grid_constant__ CgArgs<T> A) {
+__device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, const CgArgs<T>& A, SolveCtx<T>& X) {
   constexpr int NN = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[32];
-  __shared__ T bcast;
-  __shared__ int s_flag;
   const bool pc = A.precond == 1;
-  SolveCtx<T> X;
-  init_ctx<T, N>(X, smem_raw, G, A.pc.Bt, pc, max(G.Nx, G.Ny));
-  X.red = red;
-  X.bcast = &bcast;
-  X.s_flag = &s_flag;
   X.sync = A.sync;
   X.part = A.part;
   X.phase = 0;
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t stride = (size_t)X.vsize * blockDim.x;
   int flags = 0, it = 0;
   T rr = T(0), rhob = T(0), rz = T(0);
 
@@ -725,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
   if (A.rhs == nullptr) {
     for (int pass = 0; pass < 2; ++pass) {
       T s = T(0);
-      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+      for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
         s = fma(C.wq[i % NN], T(A.omega[i]) - wbar, s);
       T m = T(0);
       if (!reduce_all(X, s, m)) {
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
   // P1: y0, b, r0 = b - Ahat y0, rr0 = r0.r0, rhob = b.b.
   {
     T rrb = T(0), bbb = T(0);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = X.vrank; t < ntiles; t += X.vsize) {
       cg_tile_apply<T, N>(
           C, G, t, X,
           [&](size_t g, int k, bool interior) {
@@ -763,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
     }
   }
   if (rhob == T(0)) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.v.y + i, T(0));
+    for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.v.y + i, T(0));
     rr = T(0);
   } else {
     if (pc && !pc_apply<T, N>(C, G, A.pc, A.v.r, X, rz)) {
@@ -776,10 +780,10 @@ __global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Op
   }
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       A.psi_out[i] = double(__ldcg(A.v.y + i) * C.isw[i % NN]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (X.vrank == 0 && threadIdx.x == 0) {
     SolveStatus* st = A.status;
     st->total_iters += it;
     st->last_iters = it;
@@ -791,6 +795,23 @@ finish:
     st->last_rho = double(rr);
     st->last_rhob = double(rhob);
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+                                                     const __grid_constant__ CgArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[32];
+  __shared__ T bcast;
+  __shared__ int s_flag;
+  SolveCtx<T> X;
+  init_ctx<T, N>(X, smem_raw, G, A.pc.Bt, A.precond == 1, max(G.Nx, G.Ny));
+  X.red = red;
+  X.bcast = &bcast;
+  X.s_flag = &s_flag;
+  X.vrank = blockIdx.x;
+  X.vsize = gridDim.x;
+  cg_solve<T, N>(C, G, A, X);
 }
 
 // =========================================================================================
@@ -837,7 +858,7 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
                                                double wbar, bool from_x0, SolveCtx<double>& X, double& rr,
                                                double& bb) {
   const int ntiles = G.tilesX * G.tilesY;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = X.vrank; t < ntiles; t += X.vsize) {
     cg_tile_apply<double, N>(
         Cd, G, t, X,
         [&](size_t g, int k, bool interior) {
@@ -862,43 +883,28 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
   }
 }
 
+// The whole mixed-precision solve on the (virtual) grid of Xf / Xd (float context with the
+// staged block matrix, double context over the same region; see mixed_cg_kernel).
 template <int N>
-__global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
-                                                           const __grid_constant__ Ops2D<float, N> Cf, const Geom G,
-                                                           const __grid_constant__ MixedArgs A) {
+__device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Ops2D<float, N>& Cf, const Geom& G,
+                                            const MixedArgs& A, SolveCtx<float>& Xf, SolveCtx<double>& Xd) {
   constexpr int NN = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double redd[32];
-  __shared__ double bcd;
-  __shared__ float redf[32];
-  __shared__ float bcf;
-  __shared__ int s_flag;
   const bool pc = A.precond == 1;
-  const int Lmax = max(G.Nx, G.Ny);
-  SolveCtx<float> Xf;
-  init_ctx<float, N>(Xf, smem_raw, G, A.pc.Bt, pc, Lmax);
-  Xf.red = redf;
-  Xf.bcast = &bcf;
-  Xf.s_flag = &s_flag;
   Xf.sync = A.sync;
   Xf.part = A.partf;
   Xf.phase = 0;
-  SolveCtx<double> Xd;
-  init_ctx<double, N>(Xd, smem_raw + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
-  Xd.red = redd;
-  Xd.bcast = &bcd;
-  Xd.s_flag = &s_flag;
   Xd.sync = A.sync;
   Xd.part = A.partd;
   Xd.phase = 0;
+  int* s_flag_ptr = Xd.s_flag;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t stride = (size_t)Xd.vsize * blockDim.x;
   int flags = 0, sweeps = 0;
   long long inner = 0;
   double rr = 0.0, bb = 0.0, wbar = 0.0;
   for (int mp = 0; mp < 2; ++mp) {  // two-pass W-mean, as in cg_kernel
     double s = 0.0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       s = fma(Cd.wq[i % NN], A.omega[i] - wbar, s);
     double m = 0.0;
     if (!reduce_all(Xd, s, m)) {
@@ -918,7 +924,7 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
       }
     }
     if (bb == 0.0) {
-      for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.y + i, 0.0);
+      for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.y + i, 0.0);
       rr = 0.0;
       break;
     }
@@ -944,9 +950,9 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
       goto finish;
     }
     // y += e
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       __stcg(A.y + i, __ldcg(A.y + i) + double(__ldcg(A.v.y + i)));
-    if (!grid_barrier(A.sync, &s_flag)) {
+    if (!grid_barrier(A.sync, s_flag_ptr, Xd.vsize)) {
       flags |= kFlagTimeout;
       goto finish;
     }
@@ -955,10 +961,10 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
   if (pc && !(flags & kFlagTimeout) && !project_mean<double, N>(Cd, G, A.y, A.sumW, Xd)) flags |= kFlagTimeout;
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += stride)
+    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       A.psi_out[i] = __ldcg(A.y + i) * Cd.isw[i % NN];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (Xd.vrank == 0 && threadIdx.x == 0) {
     SolveStatus* st = A.status;
     const int it = int(inner);
     st->total_iters += it;
@@ -971,6 +977,225 @@ finish:
     st->last_rho = rr;
     st->last_rhob = bb;
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
+                                                           const __grid_constant__ Ops2D<float, N> Cf, const Geom G,
+                                                           const __grid_constant__ MixedArgs A) {
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double redd[32];
+  __shared__ double bcd;
+  __shared__ float redf[32];
+  __shared__ float bcf;
+  __shared__ int s_flag;
+  const bool pc = A.precond == 1;
+  const int Lmax = max(G.Nx, G.Ny);
+  SolveCtx<float> Xf;
+  init_ctx<float, N>(Xf, smem_raw, G, A.pc.Bt, pc, Lmax);
+  Xf.red = redf;
+  Xf.bcast = &bcf;
+  Xf.s_flag = &s_flag;
+  Xf.vrank = blockIdx.x;
+  Xf.vsize = gridDim.x;
+  SolveCtx<double> Xd;
+  init_ctx<double, N>(Xd, smem_raw + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
+  Xd.red = redd;
+  Xd.bcast = &bcd;
+  Xd.s_flag = &s_flag;
+  Xd.vrank = blockIdx.x;
+  Xd.vsize = gridDim.x;
+  mixed_solve<N>(Cd, Cf, G, A, Xf, Xd);
+}
+
+// =========================================================================================
+// Batched persistent step: many independent simulations (different grids, n, viscosities)
+// advance in one cooperative launch.  The blocks are split into groups; each group is a
+// virtual grid (its own barrier, block ranks and partial sums) that runs whole AB3 steps --
+// the RHS tile pass, the Poisson solve, the rotation of the state rings -- for the
+// simulations queued on it, one after the other.  Groups run concurrently.
+// =========================================================================================
+struct BatchSim {
+  int n, precision, precond;       // precision: 0 float64, 1 mixed (float32 RHS), 2 mixed (float64 RHS)
+  Geom Gr, Gc;                     // tiles of the RHS and of the solve
+  const void* ops_d;               // device copy of Ops2D<double, n>
+  const void* ops_f;               // device copy of Ops2D<float, n>
+  double* omega[2];
+  double* psi[3];                  // sqrt(W) psi
+  void* R[3];                      // float64, or float32 with a float32 RHS
+  int oc, p0, p1, p2, r1, r2, rfree;  // ring indices, advanced by the kernel
+  long long step;
+  double D, dt, tol2, tol_in2;
+  int maxit, max_sweeps, fixed_iters;
+  double sumW;
+  // float64 solve
+  double *r, *p0v, *p1v, *q, *part;
+  // mixed solve
+  float *rf, *fr, *fe, *fp0, *fp1, *fq, *partf;
+  SolveStatus* status;
+  PrecondArgs<double> pc;
+  PrecondArgs<float> pcf;
+};
+
+struct BatchGroup {
+  int first_block, nblocks;  // blocks [first_block, first_block + nblocks)
+  int first, count;          // simulations order[first .. first + count)
+  SyncState* sync;
+};
+
+struct BatchArgs {
+  BatchSim* sims;
+  const int* order;
+  const BatchGroup* groups;
+  int ngroups;
+  int nsteps;
+  int* error;                // first error flag of any group
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& C, int oc, int p0, int r1, int r2,
+                                          int rfree, int vrank, int vsize, unsigned char* smem) {
+  RhsArgs<T> A{};
+  A.psi = S.psi[p0];
+  A.omega_in = S.omega[oc];
+  A.omega_base = S.omega[oc];
+  A.omega_out = S.omega[oc ^ 1];
+  A.R_out = static_cast<T*>(S.R[rfree]);
+  A.hist[0] = static_cast<const T*>(S.R[r1]);
+  A.hist[1] = static_cast<const T*>(S.R[r2]);
+  A.c_new = 23.0 / 12.0;
+  A.c_hist[0] = -16.0 / 12.0;
+  A.c_hist[1] = 5.0 / 12.0;
+  A.nhist = 2;
+  A.dt = S.dt;
+  A.visc = S.D;
+  A.psi_scaled = 1;
+  const int nt = S.Gr.tilesX * S.Gr.tilesY;
+  for (int t = vrank; t < nt; t += vsize) rhs_tile<T, N>(C, S.Gr, A, t, smem);
+}
+
+// One AB3 step of simulation S on a group.  Returns false after a barrier timeout.
+template <int N>
+__device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int vrank, unsigned char* smem,
+                                           double* redd, double* bcd, float* redf, float* bcf, int* s_flag) {
+  constexpr int NN = N * N;
+  const BatchSim& S = *Sp;
+  const int oc = __ldcg(&Sp->oc), p0 = __ldcg(&Sp->p0), p1 = __ldcg(&Sp->p1), p2 = __ldcg(&Sp->p2);
+  const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), rfree = __ldcg(&Sp->rfree);
+  const Ops2D<double, N>& Cd = *static_cast<const Ops2D<double, N>*>(S.ops_d);
+  const Ops2D<float, N>& Cf = *static_cast<const Ops2D<float, N>*>(S.ops_f);
+  if (S.precision == 1)
+    batch_rhs<float, N>(S, Cf, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
+  else
+    batch_rhs<double, N>(S, Cd, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
+  if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
+  const bool pc = S.precond == 1;
+  const int Lmax = max(S.Gc.Nx, S.Gc.Ny);
+  if (S.precision == 0) {
+    CgArgs<double> A{};
+    A.omega = S.omega[oc ^ 1];
+    A.xa = S.psi[p0];
+    A.xb = S.psi[p1];
+    A.ca = 2.0;
+    A.cb = -1.0;
+    A.v = CgVectors<double>{S.psi[p2], S.r, S.p0v, S.p1v, S.q};
+    A.precond = S.precond;
+    A.pc = S.pc;
+    A.part = S.part;
+    A.sync = grp.sync;
+    A.status = S.status;
+    A.tol2 = S.tol2;
+    A.maxit = S.fixed_iters > 0 ? max(S.maxit, S.fixed_iters) : S.maxit;
+    A.fixed_iters = S.fixed_iters;
+    A.sumW = S.sumW;
+    SolveCtx<double> X;
+    init_ctx<double, N>(X, smem, S.Gc, S.pc.Bt, pc, Lmax);
+    X.red = redd;
+    X.bcast = bcd;
+    X.s_flag = s_flag;
+    X.vrank = vrank;
+    X.vsize = grp.nblocks;
+    cg_solve<double, N>(Cd, S.Gc, A, X);
+  } else {
+    MixedArgs A{};
+    A.omega = S.omega[oc ^ 1];
+    A.xa = S.psi[p0];
+    A.xb = S.psi[p1];
+    A.ca = 2.0;
+    A.cb = -1.0;
+    A.y = S.psi[p2];
+    A.rf = S.rf;
+    A.v = CgVectors<float>{S.fe, S.fr, S.fp0, S.fp1, S.fq};
+    A.precond = S.precond;
+    A.pc = S.pcf;
+    A.partd = S.part;
+    A.partf = S.partf;
+    A.sync = grp.sync;
+    A.status = S.status;
+    A.tol2 = S.tol2;
+    A.tol_in2 = S.tol_in2;
+    A.max_sweeps = S.max_sweeps;
+    A.maxit_in = S.maxit;
+    A.sumW = S.sumW;
+    SolveCtx<float> Xf;
+    init_ctx<float, N>(Xf, smem, S.Gc, S.pcf.Bt, pc, Lmax);
+    Xf.red = redf;
+    Xf.bcast = bcf;
+    Xf.s_flag = s_flag;
+    Xf.vrank = vrank;
+    Xf.vsize = grp.nblocks;
+    SolveCtx<double> Xd;
+    init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), S.Gc, nullptr, false, Lmax);
+    Xd.red = redd;
+    Xd.bcast = bcd;
+    Xd.s_flag = s_flag;
+    Xd.vrank = vrank;
+    Xd.vsize = grp.nblocks;
+    mixed_solve<N>(Cd, Cf, S.Gc, A, Xf, Xd);
+  }
+  // every block has finished the solve before the rings move
+  if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
+  if (vrank == 0 && threadIdx.x == 0) {
+    Sp->oc = oc ^ 1;
+    Sp->p0 = p2;
+    Sp->p1 = p0;
+    Sp->p2 = p1;
+    Sp->r1 = rfree;
+    Sp->r2 = r1;
+    Sp->rfree = r2;
+    Sp->step = S.step + 1;
+    __threadfence();
+  }
+  return grid_barrier(grp.sync, s_flag, grp.nblocks);
+}
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double redd[32];
+  __shared__ double bcd;
+  __shared__ float redf[32];
+  __shared__ float bcf;
+  __shared__ int s_flag;
+  int gi = 0;
+  while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.groups[gi + 1].first_block) ++gi;
+  const BatchGroup grp = A.groups[gi];
+  const int vrank = int(blockIdx.x) - grp.first_block;
+  bool ok = true;
+  for (int st = 0; st < A.nsteps && ok; ++st) {
+    for (int j = 0; j < grp.count && ok; ++j) {
+      BatchSim* S = A.sims + A.order[grp.first + j];
+      switch (S->n) {
+        case 1: ok = batch_step<1>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
+        case 2: ok = batch_step<2>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
+        case 3: ok = batch_step<3>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
+        case 4: ok = batch_step<4>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
+        case 5: ok = batch_step<5>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
+        default: ok = false;
+      }
+    }
+  }
+  if (!ok && threadIdx.x == 0) atomicCAS(A.error, 0, kFlagTimeout);
 }
 
 // =========================================================================================

@@ -11,7 +11,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(7)
-DG_FP64, DG_MIXED = 0, 1
+DG_FP64, DG_MIXED, DG_MIXED64 = 0, 1, 2
 DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
 
 ERROR_NAMES = {DG_ERR_ARG: "DG_ERR_ARG", DG_ERR_CUDA: "DG_ERR_CUDA", DG_ERR_NOMEM: "DG_ERR_NOMEM",
@@ -71,6 +71,14 @@ def _load():
         "dg_sim_invariants": (I, [P, PD, P]),
         "dg_sim_set_cg": (I, [P, D, I, I]),
         "dg_sim_set_refinement": (I, [P, D, I]),
+        "dg_batch_create": (I, [PP, I]),
+        "dg_batch_destroy": (I, [P]),
+        "dg_batch_admit": (I, [P, P, P]),
+        "dg_batch_retire": (I, [P, P]),
+        "dg_batch_size": (I, [P]),
+        "dg_batch_set_groups": (I, [P, I]),
+        "dg_batch_step": (I, [P, I, P]),
+        "dg_batch_status": (I, [P, PI, PI, ctypes.POINTER(LL), P]),
         "dg_sim_upload": (I, [P, LL, P, P, P, P, P, P]),
         "dg_sim_download": (I, [P, P, P, P]),
         "dg_sim_set_timing": (I, [P, I]),
@@ -297,6 +305,51 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             _lib.dg_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """dg_batch: simulations advanced together by one persistent, graph-captured kernel."""
+
+    def __init__(self, max_sims):
+        h = ctypes.c_void_p()
+        _check(_lib.dg_batch_create(ctypes.byref(h), int(max_sims)))
+        self.h = h
+        self.members = []
+
+    def admit(self, sim, stream=None):
+        _check(_lib.dg_batch_admit(self.h, sim.h, _stream(stream)))
+        self.members.append(sim)
+
+    def retire(self, sim):
+        _check(_lib.dg_batch_retire(self.h, sim.h))
+        self.members.remove(sim)
+
+    def set_groups(self, ngroups):
+        _check(_lib.dg_batch_set_groups(self.h, int(ngroups)))
+
+    def step(self, nsteps=1, stream=None):
+        _check(_lib.dg_batch_step(self.h, int(nsteps), _stream(stream)))
+
+    def status(self, stream=None, check=True):
+        g, ng, nl = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0)
+        rc = _lib.dg_batch_status(self.h, ctypes.byref(g), ctypes.byref(ng), ctypes.byref(nl), _stream(stream))
+        if check:
+            _check(rc)
+        return {"rc": rc, "graph": bool(g.value), "groups": ng.value, "launches": nl.value}
+
+    def __len__(self):
+        return int(_lib.dg_batch_size(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.dg_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,152 @@
+"""Continuous-batching simulation server on one GPU.
+
+Requests (cells per side N, nodes n, viscosity D, number of steps, initial field) arrive
+over time.  A request is admitted as soon as a batch slot is free and its device-memory
+footprint fits the HBM budget; admission builds its grid and simulation (initial Poisson
+solve) and takes its two RK4 start-up steps, then the request joins the batch
+(dg_batch_admit).  The GPU loop advances every admitted simulation with one persistent,
+graph-captured launch per chunk of steps (dg_batch_step); a simulation that has taken all its
+steps is retired, its latency (arrival -> completion) recorded and its memory freed, which
+admits waiting requests.  Requests that arrive while others are on the GPU therefore overlap
+with them on the device.
+
+All GPU work goes through the C ABI (paper_1311_7477_gb300.dg); this module only decides what
+runs when.
+"""
+import time
+
+import numpy as np
+
+from . import dg, workloads
+
+# device bytes per dof of one simulation (state rings, RK stages, solver and preconditioner
+# vectors, grid workspace), float64 / mixed
+BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 21 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10}
+
+
+def footprint(N, n, precision):
+    return N * N * n * n * BYTES_PER_DOF[precision]
+
+
+class Request:
+    def __init__(self, spec):
+        self.spec = spec
+        self.id = spec["id"]
+        self.arrival = spec["arrival"]
+        self.steps = spec["steps"]
+        self.admit_t = None
+        self.done_t = None
+        self.grid = None
+        self.sim = None
+        self.remaining = None
+
+    @property
+    def dof(self):
+        return self.spec["N"] ** 2 * self.spec["n"] ** 2
+
+
+class Server:
+    def __init__(self, max_active=64, hbm_budget=200e9, precision=dg.DG_MIXED, precond="twolevel", cg_tol=1e-10,
+                 chunk=8, dt_cap=2e-4, keep_results=False):
+        self.batch = dg.Batch(max_active)
+        self.max_active = max_active
+        self.budget = float(hbm_budget)
+        self.precision = precision
+        self.precond = precond
+        self.cg_tol = cg_tol
+        self.chunk = int(chunk)
+        self.dt_cap = dt_cap
+        self.keep_results = keep_results
+        self.active = []
+        self.used = 0.0
+        self.done = []
+        self.results = {}
+        self.dof_steps = 0
+
+    def _admit(self, req, now):
+        import torch
+        s = req.spec
+        g = dg.Grid(s["N"], s["N"], s["n"])
+        g.set_precond(self.precond)
+        w0 = torch.from_numpy(workloads.initial_field(dg, g, s)).cuda()
+        dt = workloads.stable_dt(dg, s["N"], s["n"], s["D"], dt_cap=self.dt_cap)
+        sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=self.precision, cg_tol=self.cg_tol, cg_maxit=100000)
+        del w0
+        req.grid, req.sim = g, sim
+        req.admit_t = now
+        steps0 = min(2, req.steps)
+        if req.steps < 2:
+            sim.step(req.steps)
+            req.remaining = 0
+        else:
+            self.batch.admit(sim)          # the two RK4 start-up steps run here
+            req.remaining = req.steps - 2
+        self.dof_steps += req.dof * steps0
+        self.used += footprint(s["N"], s["n"], self.precision)
+        self.active.append(req)
+
+    def _finish(self, req, now):
+        import torch
+        if req.sim in self.batch.members:
+            self.batch.retire(req.sim)
+        torch.cuda.synchronize()
+        req.done_t = now
+        if self.keep_results:
+            om = torch.empty(req.grid.shape, dtype=torch.float64, device="cuda")
+            ps = torch.empty_like(om)
+            req.sim.get(om, ps)
+            torch.cuda.synchronize()
+            self.results[req.id] = (om.cpu().numpy(), ps.cpu().numpy(), req.sim.status().step)
+        req.sim.close()
+        req.grid.close()
+        req.sim = req.grid = None
+        self.used -= footprint(req.spec["N"], req.spec["n"], self.precision)
+        self.active.remove(req)
+        self.done.append(req)
+
+    def run(self, trace, time_scale=1.0, clock=time.perf_counter):
+        """Serves the trace (arrival times scaled by time_scale); returns the report dict."""
+        import torch
+        pending = sorted((Request(s) for s in trace), key=lambda r: r.arrival)
+        queue = []
+        t0 = clock()
+        launches = 0
+        while pending or queue or self.active:
+            now = clock() - t0
+            while pending and pending[0].arrival * time_scale <= now:
+                queue.append(pending.pop(0))
+            # admission by free slots and by the HBM budget (FIFO)
+            while queue and len(self.active) < self.max_active:
+                r = queue[0]
+                need = footprint(r.spec["N"], r.spec["n"], self.precision)
+                if self.used + need > self.budget and self.active:
+                    break
+                queue.pop(0)
+                self._admit(r, clock() - t0)
+            for r in [r for r in self.active if r.remaining == 0]:
+                self._finish(r, clock() - t0)
+            runnable = [r for r in self.active if r.remaining > 0]
+            if not runnable:
+                if pending and not queue:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival * time_scale - (clock() - t0))))
+                continue
+            k = min(self.chunk, min(r.remaining for r in runnable))
+            self.batch.step(k)
+            launches += 1
+            for r in runnable:
+                r.remaining -= k
+                self.dof_steps += r.dof * k
+            finished = [r for r in runnable if r.remaining == 0]
+            if finished:
+                torch.cuda.synchronize()
+                for r in finished:
+                    self._finish(r, clock() - t0)
+        torch.cuda.synchronize()
+        wall = clock() - t0
+        lat = np.array([r.done_t - r.arrival * time_scale for r in self.done])
+        st = self.batch.status(check=False)
+        return {"requests": len(self.done), "wall_s": wall,
+                "mdof_steps_per_s": self.dof_steps / wall / 1e6,
+                "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                "batch_launches": launches, "batch_status": st["rc"], "graph": st["graph"]}

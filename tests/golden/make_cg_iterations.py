@@ -1,10 +1,12 @@
-"""Writes cg_iterations_shear512_n4.json: the CG iterations per Poisson solve that the FP64
-oracle itself takes on the large single-run workload (512 x 512 cells, n = 4, double shear
-layer rho = delta = 0.05, D = 1e-4, dt = 5e-4, CG tol 1e-10; two RK4 start-up steps then
-AB3).  Calls only oracle/ and the input generator.  Used to scale the bounded CPU-baseline
-sample of bench.py (oracle RHS + a few CG iterations) to one full time step.
+"""Writes cg_iterations_shear512_n4_<precond>.json: the CG iterations per Poisson solve that
+the FP64 oracle itself takes on the large single-run workload (512 x 512 cells, n = 4,
+double shear layer rho = delta = 0.05, D = 1e-4, dt = 5e-4, CG tol 1e-10; two RK4 start-up
+steps then AB3), with the given preconditioner.  Calls only oracle/ and the input
+generator.  Used to scale the bounded CPU-baseline sample of bench.py (oracle RHS + a few CG
+iterations) to one full time step.
 
-    python tests/golden/make_cg_iterations.py [nsteps]     (about an hour of CPU)
+    python tests/golden/make_cg_iterations.py [nsteps] [jacobi|twolevel]
+        (twolevel: about half an hour of CPU; jacobi: many hours)
 """
 import json
 import os
@@ -23,7 +25,7 @@ from oracle.tables import Grid  # noqa: E402
 from paper_1311_7477_gb300 import fields  # noqa: E402
 
 
-def main(nsteps=4):
+def main(nsteps=4, precond="twolevel"):
     N, n, D, dt, tol = 512, 4, 1e-4, 5e-4, 1e-10
     g = Grid(N, N, n)
     ops = Operators(g)
@@ -32,15 +34,15 @@ def main(nsteps=4):
     log = []
     orig = S.solve_poisson
 
-    def logged(ops_, omega, x0, tol_, maxit, fixed_iters=0):
+    def logged(ops_, omega, x0, tol_, maxit, fixed_iters=0, pc=None):
         t0 = time.time()
-        res = orig(ops_, omega, x0, tol_, maxit, fixed_iters)
+        res = orig(ops_, omega, x0, tol_, maxit, fixed_iters, pc)
         log.append({"iters": res.iters, "relres": res.relres, "seconds": time.time() - t0})
         print("solve", len(log), res.iters, "%.1fs" % log[-1]["seconds"], flush=True)
         return res
 
     ST.solve_poisson = logged
-    sim = ST.Simulation(ops, w0, D, dt, tol=tol, maxit=200000, K=3)
+    sim = ST.Simulation(ops, w0, D, dt, tol=tol, maxit=200000, K=3, precond=precond)
     per_step = []
     for k in range(nsteps):
         before = len(log)
@@ -50,16 +52,17 @@ def main(nsteps=4):
                          "solves": log[before:], "seconds": time.time() - t0})
     out = {
         "workload": "shear layer 512x512 cells, n=4, D=1e-4, dt=5e-4, CG tol 1e-10 (FP64 oracle)",
+        "preconditioner": precond,
         "initial_solve": log[0],
         "steps": per_step,
         "ab3_iters_mean": float(np.mean([s["solves"][0]["iters"] for s in per_step if s["kind"] == "ab3"]))
         if nsteps > 2 else None,
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cg_iterations_shear512_n4.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cg_iterations_shear512_n4_%s.json" % precond)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path)
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 4)
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 4, sys.argv[2] if len(sys.argv) > 2 else "twolevel")

@@ -1,0 +1,46 @@
+"""The continuous-batching server: requests arriving while others run are admitted into the
+batch and overlap on the device; every result must equal the same request run alone (within
+the solver tolerance), and latencies must be reported."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dg(native):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return native
+
+
+@pytest.mark.parametrize("precision", ["mixed64", "fp64"])
+def test_served_results_equal_alone(dg, precision):
+    from paper_1311_7477_gb300 import serve, workloads
+    prec = {"fp64": dg.DG_FP64, "mixed64": dg.DG_MIXED64}[precision]
+    trace = workloads.request_trace(count=8, rate=400.0, seed=11, Ns=(16, 24, 32), ns=(2, 3), steps=(3, 14))
+    srv = serve.Server(max_active=4, hbm_budget=1e9, precision=prec, precond="twolevel", cg_tol=1e-12, chunk=3,
+                       keep_results=True)
+    rep = srv.run(trace)
+    assert rep["requests"] == len(trace) and rep["batch_status"] == 0
+    assert rep["latency_p50_s"] is not None and rep["latency_p99_s"] >= rep["latency_p50_s"]
+    # requests overlapped: some were admitted before others finished
+    spans = sorted((r.admit_t, r.done_t) for r in srv.done)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    for spec in trace:
+        g = dg.Grid(spec["N"], spec["N"], spec["n"])
+        g.set_precond("twolevel")
+        w0 = torch.from_numpy(workloads.initial_field(dg, g, spec)).cuda()
+        dt = workloads.stable_dt(dg, spec["N"], spec["n"], spec["D"])
+        s = dg.Sim(g, w0, D=spec["D"], dt=dt, precision=prec, cg_tol=1e-12)
+        s.step(spec["steps"])
+        om = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        ps = torch.empty_like(om)
+        s.get(om, ps)
+        torch.cuda.synchronize()
+        wb, pb, nsteps = srv.results[spec["id"]]
+        assert nsteps == spec["steps"]
+        ew = np.linalg.norm(om.cpu().numpy() - wb) / np.linalg.norm(wb)
+        ep = np.linalg.norm(ps.cpu().numpy() - pb) / np.linalg.norm(pb)
+        assert ew < 1e-9 and ep < 1e-9, (spec, ew, ep)
