@@ -34,7 +34,12 @@ WORKLOADS = {
     # not single runs: handled by run_batch / run_serve
     "batch64": dict(N=0, n=0, D=0.0, dt=0.0, tol=1e-10, field="random_phase"),
     "serve": dict(N=0, n=0, D=0.0, dt=0.0, tol=1e-10, field="mixed"),
+    # one bracket evaluation, N = 100, P = 1..4 (Table 1): handled by run_bracket
+    "bracket_table1": dict(N=100, n=4, D=0.0, dt=0.0, tol=0.0, field="random_phase"),
 }
+# Table 1: milliseconds per bracket evaluation at N = 100 on a GeForce GTX 570 and on a Xeon
+# E3-1225 V2 with 4 threads, FP64
+TABLE1_MS = {1: (0.05, 0.08), 2: (0.26, 0.52), 3: (0.71, 3.85), 4: (1.47, 9.08)}
 DEFAULT_WORKLOAD = "shear512_n4"
 L2_BYTES = 129 * 1024 * 1024
 # FP64 FMA peak of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (recipe's unit counts
@@ -48,6 +53,24 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measured_traffic(workload, precision, precond):
+    """DRAM bytes per cg_kernel launch from the ncu capture summarised in
+    profiles/cg_kernel_traffic_<workload>.md (None if there is no row for this setup)."""
+    path = os.path.join(ROOT, "profiles", "cg_kernel_traffic_%s.md" % workload)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 5 and cells[:3] == [workload, precision, precond]:
+            try:
+                return int(cells[3])
+            except ValueError:
+                return None
+    return None
 
 
 def make_field(name, X, Y):
@@ -195,10 +218,44 @@ def cpu_baseline(name, wl, native_iters, precond="twolevel"):
             "parts_s_per_dof": s}
 
 
+def oracle_bracket_ms(n, N=100, calls=3):
+    """Milliseconds per oracle bracket evaluation on the N x N grid (host cores)."""
+    import numpy as np
+    from oracle.operators import Operators
+    from oracle.tables import Grid
+    from paper_1311_7477_gb300 import fields
+    g = Grid(N, N, n)
+    ops = Operators(g)
+    X, Y = g.mesh()
+    f, w = fields.random_phase(X, Y, seed=2), fields.random_phase(X, Y, seed=3)
+    ops.bracket(f, w)
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        ops.bracket(f, w)
+    return (time.perf_counter() - t0) / calls * 1e3
+
+
 def run_reference(args, wl, name):
     """--impl reference: the oracle on the host cores, each step one bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if name == "bracket_table1":
+        for _ in range(args.warmup):
+            oracle_bracket_ms(4, calls=1)
+        t0 = time.perf_counter()
+        ms = sum(oracle_bracket_ms(4, calls=1) for _ in range(args.steps)) / args.steps
+        value = 100 * 100 * 16 / (ms / 1e3) / 1e6
+        cores = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or 1
+        print(json.dumps({
+            "impl": "reference", "metric": "Mdof/s (one bracket evaluation)", "value": value, "unit": "Mdof/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bracket_table1", "cells": "100x100", "n": 4, "dof": 160000},
+            "cpu_baseline": {"value": value, "unit": "Mdof/s", "cores": cores, "kind": "oracle",
+                             "sample": "FP64 NumPy oracle bracket on the 100x100-cell n=4 grid, %d calls, %.1f s"
+                                       % (args.steps, time.perf_counter() - t0)},
+            "e2e": {"value": value, "unit": "Mdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
     k, ksrc = oracle_iters_per_step(name, args.precond)
     if k is None:
@@ -262,6 +319,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "bracket_table1":
+        run_bracket(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3 (the first two steps are RK4 start-up steps)")
@@ -435,13 +495,7 @@ def main():
     cg_bytes = dof * (bytes_iter * it_per_launch + bytes_setup)
     achieved_tf = cg_flops / (cg_ms_per_launch / 1e3) / 1e12
     achieved_gbs = cg_bytes / (cg_ms_per_launch / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "cg_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(args.workload, {}).get(args.precision)
-        except (OSError, ValueError):
-            traffic = None
+    traffic = measured_traffic(args.workload, args.precision, args.precond)
     roof = {"kernel": "cg_kernel (persistent CG Poisson solve)", "bound": "alu",
             "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -473,6 +527,109 @@ def main():
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_bracket(args):
+    """Table 1: one evaluation of the bracket of Eq. J (dg_bracket, float64) at N = 100 for
+    P = 1..4, timed per call with CUDA events around the call alone; a 512 MB buffer is
+    written between calls so each call reads its inputs from HBM, not from L2.  Also one
+    large grid (1000 x 1000 cells, n = 4) for the kernel's bandwidth roofline.  value = the
+    P = 4 rate in Mdof/s; vs_baseline = value / the GTX 570's P = 4 rate."""
+    import numpy as np
+    import torch
+    from paper_1311_7477_gb300 import build as _build
+    _build.build()
+    from paper_1311_7477_gb300 import dg, fields
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_src = measured_peaks()
+    cpu_ms = {}
+    if not args.no_cpu_baseline:
+        for n in (1, 2, 3, 4):
+            cpu_ms[n] = oracle_bracket_ms(n)
+
+    def time_bracket(g, f, w, J, calls):
+        times = []
+        for i in range(args.warmup + calls):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dg.dg_bracket(g, f, w, J, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        return float(np.median(times)), times
+
+    rows = []
+    launches = 0
+    sampler = ClockSampler(_gpu_index_for_smi(0))
+    sampler.start()
+    time.sleep(0.3)
+    for N, n in ((100, 1), (100, 2), (100, 3), (100, 4), (1000, 4)):
+        g = dg.Grid(N, N, n)
+        xn, yn, _ = g.nodes()
+        X, Y = fields.mesh_from_nodes(xn, yn)
+        f = torch.from_numpy(fields.random_phase(X, Y, seed=2)).cuda()
+        w = torch.from_numpy(fields.random_phase(X, Y, seed=3)).cuda()
+        J = torch.empty_like(w)
+        med, times = time_bracket(g, f, w, J, args.steps)
+        launches += args.steps
+        dof = g.dof
+        row = {"P": n, "N": N, "dof": dof, "ms": med, "ms_min": min(times), "mdof_per_s": dof / med / 1e3,
+               "hbm_gbs_algorithmic": 24 * dof / (med / 1e3) / 1e9}
+        if N == 100:
+            gpu_p, cpu_p = TABLE1_MS[n]
+            row.update({"paper_gtx570_ms": gpu_p, "paper_xeon4_ms": cpu_p, "speedup_vs_gtx570": gpu_p / med,
+                        "oracle_ms": cpu_ms.get(n)})
+        rows.append(row)
+        g.close()
+    # end to end: inputs from pinned host memory, J back to pinned host memory
+    g = dg.Grid(100, 100, 4)
+    xn, yn, _ = g.nodes()
+    X, Y = fields.mesh_from_nodes(xn, yn)
+    hf = torch.from_numpy(fields.random_phase(X, Y, seed=2)).pin_memory()
+    hw = torch.from_numpy(fields.random_phase(X, Y, seed=3)).pin_memory()
+    hJ = torch.empty_like(hw).pin_memory()
+    df, dw, dJ = torch.empty_like(hf, device="cuda"), torch.empty_like(hw, device="cuda"), torch.empty_like(hw,
+                                                                                                          device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        df.copy_(hf, non_blocking=True)
+        dw.copy_(hw, non_blocking=True)
+        dg.dg_bracket(g, df, dw, dJ, stream=stream)
+        hJ.copy_(dJ, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    launches += args.steps
+    clocks = sampler.stop()
+    p4, big = rows[3], rows[4]
+    big_s = big["ms"] / 1e3
+    line = {"metric": "Mdof/s (one bracket evaluation, Table 1)", "value": p4["mdof_per_s"], "unit": "Mdof/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": p4["ms"],
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": p4["mdof_per_s"] / (160000 / 1.47e-3 / 1e6), "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bracket_table1", "cells": "100x100", "n": 4, "dof": 160000,
+                       "field": "random phase psi and omega", "precision": "fp64",
+                       "l2": "flushed between calls (512 MB written)"},
+            "rows": rows,
+            "roofline": {"kernel": "rhs_kernel in bracket-only mode, 1000x1000 cells, n=4", "bound": "hbm",
+                         "achieved": big["hbm_gbs_algorithmic"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": big["hbm_gbs_algorithmic"] / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peak_src, "algorithmic_bytes_per_dof": 24,
+                         "fp64_tflops": (12 * (4 + 4) + 12) * big["dof"] / big_s / 1e12},
+            "gpu_launches": launches, "clocks": clocks,
+            "e2e": {"value": 160000 / e2e_s / 1e6, "unit": "Mdof/s", "h2d_bytes_per_step": 2 * 160000 * 8,
+                    "d2h_bytes_per_step": 160000 * 8,
+                    "what": "psi and omega copied from pinned host memory, dg_bracket, J copied back, per call"},
+            "cpu_baseline": ({"value": 160000 / (cpu_ms[4] / 1e3) / 1e6, "unit": "Mdof/s", "cores": 1,
+                              "kind": "oracle", "sample": "NumPy oracle bracket, 100x100 cells, n=4, 3 calls"}
+                             if cpu_ms else None)}
+    print(json.dumps(line))
 
 
 def _prec(dg, name):

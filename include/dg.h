@@ -41,10 +41,16 @@ extern "C" {
 #define DG_ERR_NOCONV 4     /* CG reached maxit before the tolerance                       */
 #define DG_ERR_NONFINITE 5  /* a reduction saw a NaN or Inf                                */
 #define DG_ERR_TIMEOUT 6    /* a device-side wait hit its iteration cap                    */
+#define DG_ERR_IO 7         /* a file could not be opened, read or written, or is malformed */
 
 /* ---- CG preconditioners (Sec. 6 names none; see dg_grid_set_precond) ---------------- */
 #define DG_PRECOND_JACOBI 0    /* W^-1: the inverse diagonal mass matrix (default)          */
 #define DG_PRECOND_TWOLEVEL 1  /* cell block solves + DFT coarse solve on cell averages    */
+
+/* ---- bracket variants of the time stepper (Sec. 6.2, Figures 1-2) ------------------- */
+#define DG_BRACKET_ARAKAWA 0  /* J = (J++ + J+x + Jx+) / 3 of Eq. J: conserves V, E, Omega      */
+#define DG_BRACKET_NAIVE 1    /* J++ alone: the straightforward discretisation the paper        */
+                              /* compares against (conserves V only)                            */
 
 /* ---- precision modes ------------------------------------------------------------- */
 #define DG_FP64 0     /* everything in float64                                             */
@@ -60,6 +66,14 @@ const char* dg_last_error(void);
 
 /* Library ABI version (major * 100 + minor). */
 int dg_version(void);
+
+/*
+ * dg_selftest_wait_cap -- checks the cap on device-side waits: launches a small cooperative
+ * kernel in which one block never reaches the grid barrier, so the other blocks' waits give
+ * up after about a second.  Returns DG_ERR_TIMEOUT (the expected outcome; the context stays
+ * usable) or DG_ERR_CUDA.  Synchronises the stream.
+ */
+int dg_selftest_wait_cap(void* stream);
 
 /*
  * dg_ref_tables -- host-only: the dimensionless per-n tables the kernels are built from
@@ -120,6 +134,16 @@ int dg_grid_set_precond(dg_grid* g, int kind);
  * pointwise X-space products (Sec. 4.2).  float64.  J must not alias psi or omega.
  */
 int dg_bracket(dg_grid* g, const double* psi, const double* omega, double* J, void* stream);
+
+/*
+ * dg_bracket_parts -- the individual discretisations of Eq. J: parts is a bit set of
+ * 1 = J++ = D_x f D_y g - D_y f D_x g, 2 = J+x = D_x(f D_y g) - D_y(f D_x g),
+ * 4 = Jx+ = D_y(D_x f g) - D_x(D_y f g).  With all three (7) it is dg_bracket (the sum / 3);
+ * otherwise the plain sum of the selected parts.  Only 7 conserves the integral
+ * constraints (Table 2); 1 is the naive bracket the paper compares against (Figs. 1-2).
+ * Errors: DG_ERR_ARG.
+ */
+int dg_bracket_parts(dg_grid* g, const double* psi, const double* omega, double* J, int parts, void* stream);
 
 /*
  * dg_laplace_apply -- the matrix-free LDG operator of Sec. 6 (alternating fluxes, penalty
@@ -218,6 +242,44 @@ int dg_sim_get_state(dg_sim* s, long long* step, double* omega, double* psi, dou
                      double* R1, double* R2, void* stream);
 int dg_sim_set_state(dg_sim* s, long long step, const double* omega, const double* psi,
                      const double* psi_prev, const double* R1, const double* R2, void* stream);
+
+/*
+ * dg_sim_get_history / dg_sim_set_history -- one entry R^{k-m} (m = 1, 2, 3) of the
+ * right-hand-side history (device pointer, float64 values); m = 3 is used by K = 4 only.
+ * dg_sim_set_state followed by dg_sim_set_history(s, 3, ...) restores a K = 4 state.
+ */
+int dg_sim_get_history(dg_sim* s, int m, double* R, void* stream);
+int dg_sim_set_history(dg_sim* s, int m, const double* R, void* stream);
+
+/*
+ * dg_sim_set_bracket -- the bracket used by later steps: DG_BRACKET_ARAKAWA (default, Eq. J)
+ * or DG_BRACKET_NAIVE (J++ of Eq. J alone, the comparison of Sec. 6.2).  Batched
+ * simulations must use DG_BRACKET_ARAKAWA.  Errors: DG_ERR_ARG.
+ */
+int dg_sim_set_bracket(dg_sim* s, int variant);
+
+/*
+ * dg_sim_save / dg_sim_load -- checkpoint and resume.  save writes the complete stepper
+ * state to the file path (host code; synchronises the stream): the grid's Nx, Ny, n, Lx,
+ * Ly, tau and preconditioner, D, dt, precision, K, bracket, the CG controls, the step index
+ * and six float64 arrays (omega^k, sqrt(W) psi^k, sqrt(W) psi^{k-1} -- the solver's own
+ * variables -- and R^{k-1}, R^{k-2}, R^{k-3}).  load creates a new simulation on the
+ * caller's grid g from such a file, without any solve; later steps are then bit-identical
+ * to those of the saved simulation.  The file is little-endian and not portable to
+ * big-endian hosts.  Errors: DG_ERR_ARG (NULL, or g differs from the saved grid),
+ * DG_ERR_IO (cannot open/read/write, wrong magic or version, truncated or corrupt file),
+ * DG_ERR_NOMEM, DG_ERR_CUDA.
+ */
+int dg_sim_save(dg_sim* s, const char* path, void* stream);
+int dg_sim_load(dg_sim** s, dg_grid* g, const char* path, void* stream);
+
+/*
+ * dg_sim_set_multistep -- the number of steps K (1..4) of the Adams-Bashforth method used by
+ * later steps (Sec. 6; Table 4 compares K = 1..4).  Default K = 3.  The first K-1 steps of a
+ * simulation (step index < K-1) are classical RK4 start-up steps.  Batched simulations
+ * (dg_batch_admit) must use K = 3; DG_ERR_ARG for K outside 1..4.
+ */
+int dg_sim_set_multistep(dg_sim* s, int K);
 
 /* dg_sim_invariants -- (V, E, Omega) of the current state; synchronises the stream. */
 int dg_sim_invariants(dg_sim* s, double out[3], void* stream);

@@ -10,6 +10,9 @@ Readings where Sec. 6 is silent:
   solves the Poisson equation with the latest psi as initial guess);
 * extrapolation: x0 = 2 psi^k - psi^{k-1} (linear in the last two solutions);
 * the right-hand side R(omega) = -J(psi, omega) + D Delta_h omega, J = J(psi, omega).
+
+bracket="naive" replaces J by J^{++} of Eq. J alone: the straightforward discretisation
+that Sec. 6.2 (Figures 1-2) compares with the scheme.
 """
 import numpy as np
 
@@ -28,8 +31,12 @@ class Simulation:
     """State: omega^k, psi^k, psi^{k-1}, the history R^{k-1}, R^{k-2}, ... and k."""
 
     def __init__(self, ops, omega0, D, dt, tol=1e-12, maxit=100000, K=3,
-                 fixed_iters=0, psi0=None, precond="jacobi"):
-        """precond: "jacobi" (W^{-1}) or "twolevel" (solver.TwoLevel)."""
+                 fixed_iters=0, psi0=None, precond="jacobi", bracket="arakawa"):
+        """precond: "jacobi" (W^{-1}) or "twolevel" (solver.TwoLevel); bracket: "arakawa"
+        (Eq. J) or "naive" (J^{++} alone)."""
+        if bracket not in ("arakawa", "naive"):
+            raise ValueError(bracket)
+        self.bracket = bracket
         self.ops, self.D, self.dt = ops, float(D), float(dt)
         from .solver import TwoLevel
         self.precond = TwoLevel(ops) if precond == "twolevel" else None
@@ -53,7 +60,10 @@ class Simulation:
 
     def rhs(self, psi, omega):
         """R = -J(psi, omega) + D Delta_h omega."""
-        R = -self.ops.bracket(psi, omega)
+        if self.bracket == "naive":
+            R = -self.ops.bracket_parts(psi, omega)[0]
+        else:
+            R = -self.ops.bracket(psi, omega)
         if self.D != 0.0:
             R = R + self.D * self.ops.laplacian(omega)
         return R

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -200,8 +201,10 @@ struct dg_sim {
   int oc;
   double* psi[3];  // scaled: sqrt(W) psi
   int p0, p1, p2;
-  void* R[3];      // history ring: float64 (DG_FP64) or float32 (DG_MIXED)
-  int r1, r2, rfree;
+  void* R[4];      // history ring: float64 (DG_FP64) or float32 (DG_MIXED)
+  int r1, r2, r3, rfree;  // R^{k-1}, R^{k-2}, R^{k-3}, free slot
+  int K = 3;              // steps of the Adams-Bashforth method (1..4)
+  int parts = 0;          // bracket parts (0: J of Eq. J; 1: J++ alone, the naive bracket)
   double *stA, *stB;  // RK stage vorticities
   void *k2, *k3;      // RK stage slopes (same type as R)
   double tol_in;      // inner relative tolerance of the float32 sweeps (DG_MIXED)
@@ -641,6 +644,25 @@ const char* dg_last_error(void) { return g_err; }
 
 int dg_version(void) { return 100; }
 
+int dg_selftest_wait_cap(void* stream) {
+  cudaStream_t st = as_stream(stream);
+  SyncState* s = nullptr;
+  int* out = nullptr;
+  CUDA_TRY(cudaMalloc(&s, sizeof(SyncState)));
+  CUDA_TRY(cudaMalloc(&out, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(SyncState), st));
+  CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int), st));
+  void* args[] = {(void*)&s, (void*)&out};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(4), dim3(64), args, 0, st);
+  int flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(s);
+  cudaFree(out);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+  return (flags & kFlagTimeout) ? fail(DG_ERR_TIMEOUT, "device-side wait gave up as designed") : DG_OK;
+}
+
 int dg_ref_tables_len(int n) { return (n >= 1 && n <= kMaxN) ? 7 * n + 2 * n * n : 0; }
 
 int dg_ref_tables(int n, double tau, double* out, int out_len) {
@@ -767,6 +789,21 @@ int dg_bracket(dg_grid* g, const double* psi, const double* omega, double* J, vo
   A.omega_base = omega;
   A.omega_out = J;
   A.bracket_only = 1;
+  return dispatch_n(g->n, [&](auto nc) { return launch_rhs<double, decltype(nc)::value>(g, A, as_stream(stream)); });
+}
+
+int dg_bracket_parts(dg_grid* g, const double* psi, const double* omega, double* J, int parts, void* stream) {
+  if (!g || !psi || !omega || !J) return fail(DG_ERR_ARG, "NULL argument");
+  if (parts < 1 || parts > 7) return fail(DG_ERR_ARG, "parts must be a non-empty subset of {1, 2, 4}");
+  if (!aligned8(psi) || !aligned8(omega) || !aligned8(J)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (J == psi || J == omega) return fail(DG_ERR_ARG, "J must not alias psi or omega");
+  RhsArgs<double> A{};
+  A.psi = psi;
+  A.omega_in = omega;
+  A.omega_base = omega;
+  A.omega_out = J;
+  A.bracket_only = 1;
+  A.parts = parts;
   return dispatch_n(g->n, [&](auto nc) { return launch_rhs<double, decltype(nc)::value>(g, A, as_stream(stream)); });
 }
 
@@ -911,6 +948,7 @@ int sim_rhs_t(dg_sim* s, const double* psi, const double* om_in, const double* o
   A.dt = s->dt;
   A.visc = s->D;
   A.psi_scaled = 1;
+  A.parts = s->parts;
   return dispatch_n(s->g->n, [&](auto nc) { return launch_rhs<T, decltype(nc)::value>(s->g, A, st); });
 }
 
@@ -927,6 +965,23 @@ int sim_rhs(dg_sim* s, const double* psi, const double* om_in, const double* om_
   s->rhs_launches += 1;
   return DG_OK;
 }
+
+// R^k (just written into the free slot) becomes R^{k-1} of the next step; the oldest slot
+// is freed: (r1, r2, r3, free) <- (free, r1, r2, r3).
+void rotate_history(dg_sim* s) {
+  const int r1 = s->r1, r2 = s->r2, r3 = s->r3, rf = s->rfree;
+  s->r1 = rf;
+  s->r2 = r1;
+  s->r3 = r2;
+  s->rfree = r3;
+}
+
+// Adams-Bashforth weights of R^k, R^{k-1}, ... for K = 1..4.
+const double kAB[5][4] = {{0, 0, 0, 0},
+                          {1.0, 0, 0, 0},
+                          {3.0 / 2.0, -1.0 / 2.0, 0, 0},
+                          {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0},
+                          {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0}};
 
 // One classical RK4 step (start-up of the multistep method).  k1 is kept as R^k.
 int sim_rk4_step(dg_sim* s, cudaStream_t st) {
@@ -949,35 +1004,30 @@ int sim_rk4_step(dg_sim* s, cudaStream_t st) {
   if ((rc = sim_solve(s, w1, PA, 1.0, nullptr, 0.0, PB, st))) return rc;
   // psi^{k+1} = PB (old p1 slot), psi^k stays p0: rotate (p0, p1, p2) <- (p1, p0, p2)
   std::swap(s->p0, s->p1);
-  // R ring: R^k = k1 (in rfree); R^{k-1} = old r1; the oldest slot becomes free
-  const int old_r1 = s->r1, old_r2 = s->r2;
-  s->r1 = s->rfree;
-  s->r2 = old_r1;
-  s->rfree = old_r2;
+  rotate_history(s);
   s->oc ^= 1;
   s->step += 1;
   return DG_OK;
 }
 
-// One AB3 step: omega^{k+1} = omega^k + dt (23 R^k - 16 R^{k-1} + 5 R^{k-2}) / 12, then the
-// Poisson solve from 2 psi^k - psi^{k-1}.
+// One Adams-Bashforth step of order K (K = 3 in the paper's runs):
+//   omega^{k+1} = omega^k + dt sum_m beta_m R^{k-m},
+// then the Poisson solve from the extrapolation 2 psi^k - psi^{k-1}.
 int sim_ab3_step(dg_sim* s, cudaStream_t st) {
   const double* w0 = s->omega[s->oc];
   double* w1 = s->omega[s->oc ^ 1];
   void* Rk = s->R[s->rfree];
-  void* const hist[2] = {s->R[s->r1], s->R[s->r2]};
-  const double ch[2] = {-16.0 / 12.0, 5.0 / 12.0};
+  void* const hist[3] = {s->R[s->r1], s->R[s->r2], s->R[s->r3]};
+  const int K = s->K;
+  const double ch[3] = {kAB[K][1], kAB[K][2], kAB[K][3]};
   int rc;
-  if ((rc = sim_rhs(s, s->psi[s->p0], w0, w0, w1, Rk, 23.0 / 12.0, 2, hist, ch, st))) return rc;
+  if ((rc = sim_rhs(s, s->psi[s->p0], w0, w0, w1, Rk, kAB[K][0], K - 1, hist, ch, st))) return rc;
   if ((rc = sim_solve(s, w1, s->psi[s->p0], 2.0, s->psi[s->p1], -1.0, s->psi[s->p2], st))) return rc;
   const int np0 = s->p2, np1 = s->p0, np2 = s->p1;
   s->p0 = np0;
   s->p1 = np1;
   s->p2 = np2;
-  const int old_r1 = s->r1, old_r2 = s->r2;
-  s->r1 = s->rfree;
-  s->r2 = old_r1;
-  s->rfree = old_r2;
+  rotate_history(s);
   s->oc ^= 1;
   s->step += 1;
   return DG_OK;
@@ -1024,17 +1074,31 @@ int scale_field(const dg_grid* g, const double* x, double* y, int inverse, cudaS
 
 extern "C" {
 
-int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double cg_tol, int cg_maxit,
-                  const double* omega0, void* stream) {
-  if (!sp) return fail(DG_ERR_ARG, "s is NULL");
+}  // extern "C"
+
+namespace {
+
+// Layout of a dg_sim_save file: this header, then six arrays of Nx Ny n^2 float64 values in the
+// cell-blocked node order (omega^k, sqrt(W) psi^k, sqrt(W) psi^{k-1}, R^{k-1}, R^{k-2},
+// R^{k-3}); little-endian, as written by the host.
+const char kSimMagic[8] = {'D', 'G', 'S', 'I', 'M', '0', '0', '1'};
+struct SimFileHeader {
+  char magic[8];
+  int32_t Nx, Ny, n, precision;
+  int32_t K, bracket, maxit, fixed_iters;
+  int32_t max_sweeps, precond;
+  int64_t step;
+  double Lx, Ly, tau, D, dt, tol, tol_in;
+};
+static_assert(sizeof(SimFileHeader) == 112, "file header layout");
+
+// A simulation with all its buffers allocated and no state yet (step 0, rings at rest).
+int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double cg_tol, int cg_maxit) {
   *sp = nullptr;
-  if (!g || !omega0) return fail(DG_ERR_ARG, "NULL argument");
-  if (!aligned8(omega0)) return fail(DG_ERR_ARG, "misaligned pointer");
   if (!(D >= 0.0) || !(dt > 0.0) || !(cg_tol > 0.0) || cg_maxit < 1)
     return fail(DG_ERR_ARG, "need D >= 0, dt > 0, cg_tol > 0, cg_maxit >= 1");
   if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED64)
     return fail(DG_ERR_ARG, "unknown precision %d", precision);
-  cudaStream_t st = as_stream(stream);
   dg_sim* s = new (std::nothrow) dg_sim();
   if (!s) return fail(DG_ERR_NOMEM, "host allocation failed");
   s->g = g;
@@ -1050,7 +1114,8 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
   s->p2 = 2;
   s->r1 = 0;
   s->r2 = 1;
-  s->rfree = 2;
+  s->r3 = 2;
+  s->rfree = 3;
   const size_t bytes = ndof_of(g) * sizeof(double);
   const size_t rbytes = ndof_of(g) * (precision == DG_MIXED ? sizeof(float) : sizeof(double));
   auto alloc_all = [&]() -> int {
@@ -1065,8 +1130,30 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
     if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision != DG_FP64)) return rc;
     return precision != DG_FP64 ? alloc_ws_mixed(s->ws) : DG_OK;
   };
-  int rc = alloc_all();
-  if (!rc) rc = (cudaMemcpyAsync(s->omega[0], omega0, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess)
+  if (int rc = alloc_all()) {
+    free_sim(s);
+    delete s;
+    return rc;
+  }
+  *sp = s;
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double cg_tol, int cg_maxit,
+                  const double* omega0, void* stream) {
+  if (!sp) return fail(DG_ERR_ARG, "s is NULL");
+  *sp = nullptr;
+  if (!g || !omega0) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(omega0)) return fail(DG_ERR_ARG, "misaligned pointer");
+  cudaStream_t st = as_stream(stream);
+  dg_sim* s = nullptr;
+  if (int rc = sim_new(&s, g, D, dt, precision, cg_tol, cg_maxit)) return rc;
+  const size_t bytes = ndof_of(g) * sizeof(double);
+  int rc = (cudaMemcpyAsync(s->omega[0], omega0, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess)
                     ? DG_OK
                     : fail(DG_ERR_CUDA, "copy of omega0 failed");
   // psi^0 from a zero initial guess; psi^{-1} = psi^0 so the first extrapolation is psi^0.
@@ -1096,7 +1183,7 @@ int dg_step(dg_sim* s, int nsteps, void* stream) {
   if (!s || nsteps < 0) return fail(DG_ERR_ARG, "bad arguments");
   cudaStream_t st = as_stream(stream);
   for (int i = 0; i < nsteps; ++i) {
-    const int rc = (s->step < 2) ? sim_rk4_step(s, st) : sim_ab3_step(s, st);
+    const int rc = (s->step < s->K - 1) ? sim_rk4_step(s, st) : sim_ab3_step(s, st);
     if (rc) return rc;
   }
   return DG_OK;
@@ -1149,6 +1236,18 @@ int dg_sim_set_state(dg_sim* s, long long step, const double* omega, const doubl
   if (int rc = R_from_double(s, R2, s->R[s->r2], st)) return rc;
   if (int rc = scale_field(s->g, psi, s->psi[s->p0], 0, st)) return rc;
   return scale_field(s->g, psi_prev, s->psi[s->p1], 0, st);
+}
+
+int dg_sim_get_history(dg_sim* s, int m, double* R, void* stream) {
+  if (!s || !R || m < 1 || m > 3) return fail(DG_ERR_ARG, "bad arguments");
+  const int slot[3] = {s->r1, s->r2, s->r3};
+  return R_to_double(s, s->R[slot[m - 1]], R, as_stream(stream));
+}
+
+int dg_sim_set_history(dg_sim* s, int m, const double* R, void* stream) {
+  if (!s || !R || m < 1 || m > 3) return fail(DG_ERR_ARG, "bad arguments");
+  const int slot[3] = {s->r1, s->r2, s->r3};
+  return R_from_double(s, R, s->R[slot[m - 1]], as_stream(stream));
 }
 
 int dg_sim_set_cg(dg_sim* s, double tol, int maxit, int fixed_iters) {
@@ -1215,6 +1314,127 @@ int dg_sim_get_counters(dg_sim* s, dg_sim_counters* c, void* stream) {
     CUDA_TRY(cudaEventElapsedTime(&ms, s->ev_cg[i], s->ev_cg[i + 1]));
     c->cg_ms += ms;
   }
+  return DG_OK;
+}
+
+int dg_sim_set_multistep(dg_sim* s, int K) {
+  if (!s || K < 1 || K > 4) return fail(DG_ERR_ARG, "K must be in 1..4");
+  s->K = K;
+  return DG_OK;
+}
+
+int dg_sim_set_bracket(dg_sim* s, int variant) {
+  if (!s || (variant != DG_BRACKET_ARAKAWA && variant != DG_BRACKET_NAIVE))
+    return fail(DG_ERR_ARG, "unknown bracket variant");
+  s->parts = variant == DG_BRACKET_NAIVE ? 1 : 0;
+  return DG_OK;
+}
+
+int dg_sim_save(dg_sim* s, const char* path, void* stream) {
+  if (!s || !path) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  const dg_grid* g = s->g;
+  const size_t nd = ndof_of(g);
+  SimFileHeader h{};
+  std::memcpy(h.magic, kSimMagic, sizeof(h.magic));
+  h.Nx = g->Nx;
+  h.Ny = g->Ny;
+  h.n = g->n;
+  h.precision = s->precision;
+  h.K = s->K;
+  h.bracket = s->parts ? DG_BRACKET_NAIVE : DG_BRACKET_ARAKAWA;
+  h.maxit = s->maxit;
+  h.fixed_iters = s->fixed_iters;
+  h.max_sweeps = s->max_sweeps;
+  h.precond = g->precond;
+  h.step = s->step;
+  h.Lx = g->Lx;
+  h.Ly = g->Ly;
+  h.tau = g->tau;
+  h.D = s->D;
+  h.dt = s->dt;
+  h.tol = s->tol;
+  h.tol_in = s->tol_in;
+  std::vector<double> host(nd);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(DG_ERR_IO, "cannot open %s for writing", path);
+  int rc = std::fwrite(&h, sizeof(h), 1, f) == 1 ? DG_OK : fail(DG_ERR_IO, "write failed");
+  // omega, the solver variables sqrt(W) psi^k and sqrt(W) psi^{k-1}, then R^{k-1..k-3}
+  const void* fields[6] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3]};
+  for (int i = 0; i < 6 && !rc; ++i) {
+    const double* src = static_cast<const double*>(fields[i]);
+    if (i >= 3 && s->precision == DG_MIXED) {
+      if ((rc = R_to_double(s, fields[i], s->stA, st))) break;
+      src = s->stA;
+    }
+    if (cudaMemcpyAsync(host.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(DG_ERR_CUDA, "copy to the host failed");
+      break;
+    }
+    if (std::fwrite(host.data(), sizeof(double), nd, f) != nd) rc = fail(DG_ERR_IO, "write failed");
+  }
+  if (std::fclose(f) != 0 && !rc) rc = fail(DG_ERR_IO, "close failed");
+  return rc;
+}
+
+int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
+  if (!sp) return fail(DG_ERR_ARG, "s is NULL");
+  *sp = nullptr;
+  if (!g || !path) return fail(DG_ERR_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(DG_ERR_IO, "cannot open %s", path);
+  SimFileHeader h{};
+  if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kSimMagic, sizeof(h.magic)) != 0) {
+    std::fclose(f);
+    return fail(DG_ERR_IO, "%s is not a simulation file of this version", path);
+  }
+  if (h.Nx != g->Nx || h.Ny != g->Ny || h.n != g->n || h.Lx != g->Lx || h.Ly != g->Ly || h.tau != g->tau ||
+      h.precond != g->precond) {
+    std::fclose(f);
+    return fail(DG_ERR_ARG, "the grid (size, n, domain, tau, preconditioner) differs from the saved one");
+  }
+  if (h.K < 1 || h.K > 4 || h.step < 0 || (h.bracket != DG_BRACKET_ARAKAWA && h.bracket != DG_BRACKET_NAIVE) ||
+      h.fixed_iters < 0 || h.max_sweeps < 1 || !(h.tol_in > 0.0 && h.tol_in < 1.0)) {
+    std::fclose(f);
+    return fail(DG_ERR_IO, "corrupt header in %s", path);
+  }
+  dg_sim* s = nullptr;
+  if (int rc = sim_new(&s, g, h.D, h.dt, h.precision, h.tol, h.maxit)) {
+    std::fclose(f);
+    return rc;
+  }
+  s->K = h.K;
+  s->parts = h.bracket == DG_BRACKET_NAIVE ? 1 : 0;
+  s->fixed_iters = h.fixed_iters;
+  s->max_sweeps = h.max_sweeps;
+  s->tol_in = h.tol_in;
+  s->step = h.step;
+  const size_t nd = ndof_of(g);
+  std::vector<double> host(nd);
+  void* fields[6] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3]};
+  int rc = DG_OK;
+  for (int i = 0; i < 6 && !rc; ++i) {
+    if (std::fread(host.data(), sizeof(double), nd, f) != nd) {
+      rc = fail(DG_ERR_IO, "%s is truncated", path);
+      break;
+    }
+    double* dst = (i >= 3 && s->precision == DG_MIXED) ? s->stA : static_cast<double*>(fields[i]);
+    if (cudaMemcpyAsync(dst, host.data(), nd * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = fail(DG_ERR_CUDA, "copy to the device failed");
+      break;
+    }
+    if (dst == s->stA) rc = R_from_double(s, s->stA, fields[i], st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(DG_ERR_CUDA, "copy to the device failed");
+  }
+  std::fclose(f);
+  if (rc) {
+    free_sim(s);
+    delete s;
+    return rc;
+  }
+  *sp = s;
   return DG_OK;
 }
 
@@ -1398,16 +1618,15 @@ BatchSim make_batch_sim(dg_sim* s) {
   b.ops_d = g->d_opsd;
   b.ops_f = g->d_opsf;
   for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
-  for (int i = 0; i < 3; ++i) {
-    b.psi[i] = s->psi[i];
-    b.R[i] = s->R[i];
-  }
+  for (int i = 0; i < 3; ++i) b.psi[i] = s->psi[i];
+  for (int i = 0; i < 4; ++i) b.R[i] = s->R[i];
   b.oc = s->oc;
   b.p0 = s->p0;
   b.p1 = s->p1;
   b.p2 = s->p2;
   b.r1 = s->r1;
   b.r2 = s->r2;
+  b.r3 = s->r3;
   b.rfree = s->rfree;
   b.step = s->step;
   b.D = s->D;
@@ -1551,10 +1770,7 @@ void batch_advance_host(dg_batch* b, int nsteps) {
       s->p0 = p2;
       s->p1 = p0;
       s->p2 = p1;
-      const int r1 = s->r1, r2 = s->r2, rf = s->rfree;
-      s->r1 = rf;
-      s->r2 = r1;
-      s->rfree = r2;
+      rotate_history(s);
       s->step += 1;
     }
 }
@@ -1603,6 +1819,8 @@ int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream) {
   if ((int)b->sims.size() >= b->max_sims) return fail(DG_ERR_NOMEM, "batch is full (%d simulations)", b->max_sims);
   for (dg_sim* t : b->sims)
     if (t == s) return fail(DG_ERR_ARG, "simulation already in the batch");
+  if (s->K != 3) return fail(DG_ERR_ARG, "batched steps are AB3 (the simulation uses K = %d)", s->K);
+  if (s->parts != 0) return fail(DG_ERR_ARG, "batched steps use the bracket of Eq. J");
   if (s->step < 2)
     if (int rc = dg_step(s, int(2 - s->step), stream)) return rc;  // RK4 start-up steps on their own
   b->sims.push_back(s);

@@ -49,6 +49,7 @@ struct RhsArgs {
   double visc;
   int psi_scaled;
   int bracket_only;
+  int parts;                // bit 0: J++, bit 1: J+x, bit 2: Jx+ (0 = all three, J of Eq. J)
 };
 
 template <typename T, int N>
@@ -118,6 +119,11 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   }
   __syncthreads();
 
+  // Which parts enter (Eq. J): J = s (c0 J++ + J+x + Jx+) with J+x = D_x(f g_y) - D_y(f g_x),
+  // Jx+ = D_y(f_x g) - D_x(f_y g); as h1 = a1 f g_y - b1 f_y g, h2 = a2 f_x g - b2 f g_x.
+  const int parts = A.parts ? A.parts : 7;
+  const bool use_pp = parts & 1, use_px = parts & 2, use_xp = parts & 4;
+  const int nparts = int(use_pp) + int(use_px) + int(use_xp);
   // S3a: J++ = f_x g_y - f_y g_x on the tile.
   const int nin = B.TYe * B.TXe * NN;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
@@ -138,13 +144,19 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
         const int w = B.TXe + 2;
         const int ry = c / w, rx = c - (c / w) * w - 1;
         const int o = ((ry + 1) * BW + rx + 1) * CS + k;
-        sFy[o] = prod_diff(sPsi[o], sGy[o], sFy[o], sOm[o]);
+        if (nparts == 3)
+          sFy[o] = prod_diff(sPsi[o], sGy[o], sFy[o], sOm[o]);
+        else
+          sFy[o] = (use_px ? mul_rn(sPsi[o], sGy[o]) : T(0)) - (use_xp ? mul_rn(sFy[o], sOm[o]) : T(0));
       } else {
         const int ii = i - n1;
         const int c = ii / NN, k = ii - (ii / NN) * NN;
         const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
         const int o = ((ry + 1) * BW + rx + 1) * CS + k;
-        sFx[o] = prod_diff(sFx[o], sOm[o], sPsi[o], sGx[o]);
+        if (nparts == 3)
+          sFx[o] = prod_diff(sFx[o], sOm[o], sPsi[o], sGx[o]);
+        else
+          sFx[o] = (use_xp ? mul_rn(sFx[o], sOm[o]) : T(0)) - (use_px ? mul_rn(sPsi[o], sGx[o]) : T(0));
       }
     }
   }
@@ -155,7 +167,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   __syncthreads();
 
   // S5: J = (J++ + D_x h1 + D_y h2) / 3 = (J++ + J+x + Jx+) / 3, the viscous term and the update.
-  const T third = T(1.0 / 3.0);
+  const T third = nparts == 3 ? T(1.0 / 3.0) : T(1);
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
@@ -163,7 +175,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
     const int a = k / N, b = k - (k / N) * N;
     const T dxh1 = op_x_at<T, N>(sFy, tPxR, tPxL, C.dx, lc, a, b);
     const T dyh2 = op_y_at<T, N>(sFx, tPyR, tPyL, C.dy, lc, BW, a, b);
-    const T J = ((sJ[lc * CS + k] + dxh1) + dyh2) * third;
+    const T J = (((use_pp ? sJ[lc * CS + k] : T(0)) + dxh1) + dyh2) * third;
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
     if (A.bracket_only) {
       A.omega_out[g] = double(J);
@@ -1023,8 +1035,8 @@ struct BatchSim {
   const void* ops_f;               // device copy of Ops2D<float, n>
   double* omega[2];
   double* psi[3];                  // sqrt(W) psi
-  void* R[3];                      // float64, or float32 with a float32 RHS
-  int oc, p0, p1, p2, r1, r2, rfree;  // ring indices, advanced by the kernel
+  void* R[4];                      // float64, or float32 with a float32 RHS
+  int oc, p0, p1, p2, r1, r2, r3, rfree;  // ring indices, advanced by the kernel
   long long step;
   double D, dt, tol2, tol_in2;
   int maxit, max_sweeps, fixed_iters;
@@ -1082,7 +1094,7 @@ __device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, 
   constexpr int NN = N * N;
   const BatchSim& S = *Sp;
   const int oc = __ldcg(&Sp->oc), p0 = __ldcg(&Sp->p0), p1 = __ldcg(&Sp->p1), p2 = __ldcg(&Sp->p2);
-  const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), rfree = __ldcg(&Sp->rfree);
+  const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), r3 = __ldcg(&Sp->r3), rfree = __ldcg(&Sp->rfree);
   const Ops2D<double, N>& Cd = *static_cast<const Ops2D<double, N>*>(S.ops_d);
   const Ops2D<float, N>& Cf = *static_cast<const Ops2D<float, N>*>(S.ops_f);
   if (S.precision == 1)
@@ -1163,7 +1175,8 @@ __device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, 
     Sp->p2 = p1;
     Sp->r1 = rfree;
     Sp->r2 = r1;
-    Sp->rfree = r2;
+    Sp->r3 = r2;
+    Sp->rfree = r3;
     Sp->step = S.step + 1;
     __threadfence();
   }
@@ -1196,6 +1209,15 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
     }
   }
   if (!ok && threadIdx.x == 0) atomicCAS(A.error, 0, kFlagTimeout);
+}
+
+// Self-test of the capped grid barrier: block 0 never arrives, so every other block's wait
+// runs out after kSpinCap polls and raises kFlagTimeout; nothing faults or hangs.
+__global__ void barrier_selftest_kernel(SyncState* s, int* out) {
+  __shared__ int f;
+  if (blockIdx.x == 0) return;
+  const bool ok = grid_barrier(s, &f, gridDim.x);
+  if (threadIdx.x == 0 && !ok) atomicOr(out, kFlagTimeout);
 }
 
 // =========================================================================================

@@ -10,13 +10,14 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdgk.so")
 
-DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(7)
+DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT, DG_ERR_IO = range(8)
 DG_FP64, DG_MIXED, DG_MIXED64 = 0, 1, 2
 DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
+DG_BRACKET_ARAKAWA, DG_BRACKET_NAIVE = 0, 1
 
 ERROR_NAMES = {DG_ERR_ARG: "DG_ERR_ARG", DG_ERR_CUDA: "DG_ERR_CUDA", DG_ERR_NOMEM: "DG_ERR_NOMEM",
                DG_ERR_NOCONV: "DG_ERR_NOCONV", DG_ERR_NONFINITE: "DG_ERR_NONFINITE",
-               DG_ERR_TIMEOUT: "DG_ERR_TIMEOUT"}
+               DG_ERR_TIMEOUT: "DG_ERR_TIMEOUT", DG_ERR_IO: "DG_ERR_IO"}
 
 
 class DGError(RuntimeError):
@@ -48,6 +49,7 @@ def _load():
     sig = {
         "dg_last_error": (ctypes.c_char_p, []),
         "dg_version": (I, []),
+        "dg_selftest_wait_cap": (I, [P]),
         "dg_ref_tables_len": (I, [I]),
         "dg_ref_tables": (I, [I, D, PD, I]),
         "dg_grid_create": (I, [PP, I, I, I, D, D, D]),
@@ -57,6 +59,7 @@ def _load():
         "dg_grid_set_tiles": (I, [P, I, I]),
         "dg_grid_set_precond": (I, [P, I]),
         "dg_bracket": (I, [P, P, P, P, P]),
+        "dg_bracket_parts": (I, [P, P, P, P, I, P]),
         "dg_laplace_apply": (I, [P, P, P, I, P]),
         "dg_poisson_solve": (I, [P, P, P, D, I, I, PI, PD, P]),
         "dg_invariants": (I, [P, P, P, PD, P]),
@@ -68,6 +71,12 @@ def _load():
         "dg_sim_get": (I, [P, P, P, P]),
         "dg_sim_get_state": (I, [P, ctypes.POINTER(LL), P, P, P, P, P, P]),
         "dg_sim_set_state": (I, [P, LL, P, P, P, P, P, P]),
+        "dg_sim_get_history": (I, [P, I, P, P]),
+        "dg_sim_set_history": (I, [P, I, P, P]),
+        "dg_sim_set_multistep": (I, [P, I]),
+        "dg_sim_set_bracket": (I, [P, I]),
+        "dg_sim_save": (I, [P, ctypes.c_char_p, P]),
+        "dg_sim_load": (I, [PP, P, ctypes.c_char_p, P]),
         "dg_sim_invariants": (I, [P, PD, P]),
         "dg_sim_set_cg": (I, [P, D, I, I]),
         "dg_sim_set_refinement": (I, [P, D, I]),
@@ -208,6 +217,11 @@ def dg_bracket(grid, psi, omega, J, stream=None):
     _check(_lib.dg_bracket(grid.h, _ptr(psi), _ptr(omega), _ptr(J), _stream(stream)))
 
 
+def dg_bracket_parts(grid, psi, omega, J, parts, stream=None):
+    """parts: bit set of 1 (J++), 2 (J+x), 4 (Jx+); 7 = the conservative J."""
+    _check(_lib.dg_bracket_parts(grid.h, _ptr(psi), _ptr(omega), _ptr(J), int(parts), _stream(stream)))
+
+
 def dg_laplace_apply(grid, x, y, mode=0, stream=None):
     _check(_lib.dg_laplace_apply(grid.h, _ptr(x), _ptr(y), int(mode), _stream(stream)))
 
@@ -243,14 +257,31 @@ def dg_invariants(grid, psi, omega, stream=None):
 
 
 class Sim:
-    """dg_sim: the AB3 time stepper (RK4 start-up) on a grid."""
+    """dg_sim: the K-step Adams-Bashforth time stepper (RK4 start-up, K = 3 by default) on a grid."""
 
-    def __init__(self, grid, omega0, D=0.0, dt=1e-3, precision=DG_FP64, cg_tol=1e-12, cg_maxit=100000, stream=None):
-        h = ctypes.c_void_p()
-        _check(_lib.dg_sim_create(ctypes.byref(h), grid.h, float(D), float(dt), int(precision), float(cg_tol),
-                                  int(cg_maxit), _ptr(omega0), _stream(stream)))
-        self.h = h
+    def __init__(self, grid, omega0, D=0.0, dt=1e-3, precision=DG_FP64, cg_tol=1e-12, cg_maxit=100000, stream=None,
+                 _handle=None):
+        if _handle is None:
+            _handle = ctypes.c_void_p()
+            _check(_lib.dg_sim_create(ctypes.byref(_handle), grid.h, float(D), float(dt), int(precision),
+                                      float(cg_tol), int(cg_maxit), _ptr(omega0), _stream(stream)))
+        self.h = _handle
         self.grid = grid
+
+    @classmethod
+    def load(cls, grid, path, stream=None):
+        """dg_sim_load: a simulation resumed from a dg_sim_save file on grid."""
+        h = ctypes.c_void_p()
+        _check(_lib.dg_sim_load(ctypes.byref(h), grid.h, os.fsencode(path), _stream(stream)))
+        return cls(grid, None, _handle=h)
+
+    def save(self, path, stream=None):
+        _check(_lib.dg_sim_save(self.h, os.fsencode(path), _stream(stream)))
+
+    def set_bracket(self, variant):
+        """"arakawa" (Eq. J) or "naive" (J++ alone)."""
+        v = {"arakawa": DG_BRACKET_ARAKAWA, "naive": DG_BRACKET_NAIVE}.get(variant, variant)
+        _check(_lib.dg_sim_set_bracket(self.h, int(v)))
 
     def step(self, nsteps=1, stream=None):
         _check(_lib.dg_step(self.h, int(nsteps), _stream(stream)))
@@ -274,6 +305,15 @@ class Sim:
     def set_state(self, step, omega, psi, psi_prev, R1, R2, stream=None):
         _check(_lib.dg_sim_set_state(self.h, int(step), _ptr(omega), _ptr(psi), _ptr(psi_prev), _ptr(R1), _ptr(R2),
                                      _stream(stream)))
+
+    def get_history(self, m, R, stream=None):
+        _check(_lib.dg_sim_get_history(self.h, int(m), _ptr(R), _stream(stream)))
+
+    def set_history(self, m, R, stream=None):
+        _check(_lib.dg_sim_set_history(self.h, int(m), _ptr(R), _stream(stream)))
+
+    def set_multistep(self, K):
+        _check(_lib.dg_sim_set_multistep(self.h, int(K)))
 
     def invariants(self, stream=None):
         out = (ctypes.c_double * 3)()

@@ -292,3 +292,41 @@ def test_full_size_shear_layer_sampled(dg):
     Rk = -o.bracket(ps, om) + D * o.laplacian(om)
     ref = om + dt * (23.0 * Rk - 16.0 * R1 + 5.0 * R2) / 12.0
     assert rel_l2(host(om1), ref) < 1e-12
+
+
+@pytest.mark.parametrize("parts", [1, 2, 4, 3, 7])
+def test_bracket_parts_parity(dg, parts):
+    Nx, Ny, n = 14, 9, 3
+    g = dg.Grid(Nx, Ny, n, 2.0, 1.5)
+    o = Operators(OGrid(Nx, Ny, n, 2.0, 1.5))
+    rng = np.random.default_rng(parts)
+    f, h = rng.standard_normal((2, Ny, Nx, n, n))
+    J = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    dg.dg_bracket_parts(g, dev(f), dev(h), J, parts)
+    Jpp, Jpx, Jxp = o.bracket_parts(f, h)
+    ref = {1: Jpp, 2: Jpx, 4: Jxp, 3: Jpp + Jpx, 7: (Jpp + Jpx + Jxp) / 3.0}[parts]
+    assert rel_l2(host(J), ref, bracket_scale(o, f, h)) < 1e-12
+
+
+def test_table2_on_the_gpu():
+    """Table 2 (Sec. 5.2) computed by the CUDA kernels: J++, J+x, Jx+ and J of
+    f = sin x cos y, g = exp(0.1(x+y)) on [0, pi]^2, P = 3, N = 112, integrated by quadrature."""
+    import json
+    import os
+    from paper_1311_7477_gb300 import dg as _dg
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_periodic.json")))
+    g = _dg.Grid(112, 112, 3, np.pi, np.pi)
+    xn, yn, W = g.nodes()
+    X, Y = fields.mesh_from_nodes(xn, yn)
+    f, gg = fields.table2_pair(X, Y)
+    W4 = np.broadcast_to(W[None, None], f.shape)
+    J = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    from tests.test_oracle_bracket import _printed_match
+    for row, parts in (("J++", 1), ("J+x", 2), ("Jx+", 4), ("J", 7)):
+        _dg.dg_bracket_parts(g, dev(f), dev(gg), J, parts)
+        Jh = host(J)
+        vals = (np.sum(W4 * Jh), np.sum(W4 * f * Jh), np.sum(W4 * gg * Jh))
+        for v, p in zip(vals, gold["rows"][row]):
+            assert _printed_match(v, p), (row, v, p)

@@ -1,9 +1,11 @@
 """Pins for the oracle's time stepper (Sec. 6): Tables 3 and 4 and the invariants.
 
-* Table 4, Lamb dipole, K = 1: every printed digit of eps_Omega and eps_E (10 and 20
+* Table 4, Lamb dipole, K = 1: every printed digit of eps_Omega and eps_E (10 to 80
   steps).  This fixes E = 1/2 <psi, omega>_W, Omega = 1/2 <omega, omega>_W, the bracket
   and the tau = 0 LDG Poisson operator at P = 1.
-* Table 4, K = 3 with RK4 start-up steps: within 10 percent (start-up unspecified).
+* Table 4, K = 2 and K = 3 with RK4 start-up steps: within 3 and 10 percent (start-up
+  unspecified).  The printed K = 4 rows are not reproduced by RK4 start-up steps (their
+  Omega column does not fall at order 4 either); K = 4 is left unpinned against them.
 * Table 3, P = 1, D = 0: the error is exactly zero, as printed (Poisson is solved exactly
   and the bracket vanishes); P = 1, D = 0.01 and P = 2, D = 0: the printed orders.
 * Vorticity V is conserved to roundoff in every step (linear scheme, Eq. average1).
@@ -28,7 +30,7 @@ def _lamb_run(K, steps):
     ops = Operators(g)
     X, Y = g.mesh()
     w0 = fields.lamb_dipole(X, Y)
-    sim = Simulation(ops, w0, 0.0, 0.01 / steps, tol=1e-11, K=K)
+    sim = Simulation(ops, w0, 0.0, 0.01 / steps, tol=1e-13, K=K, precond="twolevel")
     V0, E0, O0 = sim.invariants()
     sim.step(steps)
     V, E, O = sim.invariants()
@@ -36,7 +38,7 @@ def _lamb_run(K, steps):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("steps", [10, 20])
+@pytest.mark.parametrize("steps", [10, 20, 40, 80])
 def test_table4_K1_printed_digits(steps):
     gold = json.load(open(os.path.join(GOLD, "table4_lamb.json")))["K1"][str(steps)]
     eO, eE, V = _lamb_run(1, steps)
@@ -46,7 +48,17 @@ def test_table4_K1_printed_digits(steps):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("steps", [10, 20])
+@pytest.mark.parametrize("steps", [10, 20, 40, 80])
+def test_table4_K2_rk4_startup(steps):
+    gold = json.load(open(os.path.join(GOLD, "table4_lamb.json")))["K2"][str(steps)]
+    eO, eE, V = _lamb_run(2, steps)
+    assert abs(eO / float(gold["eps_Omega"]) - 1) < 0.03
+    assert abs(eE / float(gold["eps_E"]) - 1) < 0.03
+    assert abs(V) < 1e-14
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("steps", [10, 40])
 def test_table4_K3_rk4_startup(steps):
     gold = json.load(open(os.path.join(GOLD, "table4_lamb.json")))["K3"][str(steps)]
     eO, eE, V = _lamb_run(3, steps)
@@ -117,3 +129,24 @@ def test_energy_enstrophy_drift_third_order():
     for i in range(2):
         ratio = drifts[0][i] / drifts[1][i]
         assert ratio > 2.0 ** 3 * 0.7, (drifts, ratio)
+
+
+def test_naive_bracket_stepper_drifts_at_the_space_error():
+    """With J^{++} alone (the comparison of Sec. 6.2) V is still conserved each step (Table 2:
+    int J^{++} = 0), but E and Omega drift through the space discretisation: the drift no
+    longer falls as dt^3 and exceeds the scheme's by orders of magnitude."""
+    out = {}
+    for bracket in ("arakawa", "naive"):
+        for dt, steps in ((8e-3, 10), (4e-3, 20)):
+            g = Grid(10, 10, 3)
+            ops = Operators(g)
+            X, Y = g.mesh()
+            sim = Simulation(ops, fields.random_phase(X, Y, seed=3, kmax=6), 0.0, dt, tol=1e-13, bracket=bracket)
+            V0, E0, O0 = sim.invariants()
+            sim.step(steps)
+            V, E, O = sim.invariants()
+            assert abs(V - V0) < 1e-13 * np.abs(sim.omega).max()
+            out[(bracket, dt)] = (abs(E - E0) / E0, abs(O - O0) / O0)
+    for i in range(2):
+        assert out[("naive", 8e-3)][i] / out[("naive", 4e-3)][i] < 2.0
+        assert out[("naive", 4e-3)][i] > 100.0 * out[("arakawa", 4e-3)][i], out
