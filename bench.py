@@ -55,17 +55,17 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def measured_traffic(workload, precision, precond):
-    """DRAM bytes per cg_kernel launch from the ncu capture summarised in
-    profiles/cg_kernel_traffic_<workload>.md (None if there is no row for this setup)."""
-    path = os.path.join(ROOT, "profiles", "cg_kernel_traffic_%s.md" % workload)
+def measured_traffic(kernel, workload, precision, variant):
+    """DRAM bytes per launch of `kernel` from the ncu capture summarised in
+    profiles/<kernel>_traffic_<workload>.md (None if there is no row for this setup)."""
+    path = os.path.join(ROOT, "profiles", "%s_traffic_%s.md" % (kernel, workload))
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     for line in lines:
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) == 5 and cells[:3] == [workload, precision, precond]:
+        if len(cells) == 5 and cells[:3] == [workload, precision, variant]:
             try:
                 return int(cells[3])
             except ValueError:
@@ -495,7 +495,7 @@ def main():
     cg_bytes = dof * (bytes_iter * it_per_launch + bytes_setup)
     achieved_tf = cg_flops / (cg_ms_per_launch / 1e3) / 1e12
     achieved_gbs = cg_bytes / (cg_ms_per_launch / 1e3) / 1e9
-    traffic = measured_traffic(args.workload, args.precision, args.precond)
+    traffic = measured_traffic("cg_kernel", args.workload, args.precision, args.precond)
     roof = {"kernel": "cg_kernel (persistent CG Poisson solve)", "bound": "alu",
             "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -609,6 +609,7 @@ def run_bracket(args):
     clocks = sampler.stop()
     p4, big = rows[3], rows[4]
     big_s = big["ms"] / 1e3
+    big_tf = (12 * (4 + 4) + 12) * big["dof"] / big_s / 1e12
     line = {"metric": "Mdof/s (one bracket evaluation, Table 1)", "value": p4["mdof_per_s"], "unit": "Mdof/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": p4["ms"],
             "higher_is_better": True, "scaling": "weak",
@@ -617,11 +618,15 @@ def run_bracket(args):
                        "field": "random phase psi and omega", "precision": "fp64",
                        "l2": "flushed between calls (512 MB written)"},
             "rows": rows,
-            "roofline": {"kernel": "rhs_kernel in bracket-only mode, 1000x1000 cells, n=4", "bound": "hbm",
-                         "achieved": big["hbm_gbs_algorithmic"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": big["hbm_gbs_algorithmic"] / peaks["hbm_gbs"], "traffic": None,
-                         "peak_source": peak_src, "algorithmic_bytes_per_dof": 24,
-                         "fp64_tflops": (12 * (4 + 4) + 12) * big["dof"] / big_s / 1e12},
+            "roofline": {"kernel": "rhs_kernel in bracket-only mode, 1000x1000 cells, n=4", "bound": "alu",
+                         "achieved": big_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": big_tf / FP64_PEAK_TFLOPS,
+                         "traffic": measured_traffic("rhs_kernel", "bracket1000_n4", "fp64", "bracket-only"),
+                         "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz",
+                         "algorithmic_per_dof": {"flops": 12 * (4 + 4) + 12, "bytes": 24},
+                         "hbm": {"achieved": big["hbm_gbs_algorithmic"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": big["hbm_gbs_algorithmic"] / peaks["hbm_gbs"],
+                                 "peak_source": peak_src}},
             "gpu_launches": launches, "clocks": clocks,
             "e2e": {"value": 160000 / e2e_s / 1e6, "unit": "Mdof/s", "h2d_bytes_per_step": 2 * 160000 * 8,
                     "d2h_bytes_per_step": 160000 * 8,

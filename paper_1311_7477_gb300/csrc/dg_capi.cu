@@ -511,7 +511,7 @@ PrecondArgs<float> pc_args_f(const dg_grid* g, const Workspace& w) {
 template <typename T, int N>
 int launch_rhs(const dg_grid* g, const RhsArgs<T>& A, cudaStream_t st) {
   const Geom G = geom_of(g, g->rTY, g->rTX);
-  const size_t smem = rhs_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  const size_t smem = table_bytes<Ops2D<T, N>>() + rhs_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
   if (int rc = set_smem(rhs_kernel<T, N>, smem)) return rc;
   rhs_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, A);
   CUDA_TRY(cudaGetLastError());
@@ -521,7 +521,7 @@ int launch_rhs(const dg_grid* g, const RhsArgs<T>& A, cudaStream_t st) {
 template <typename T, int N>
 int launch_apply(const dg_grid* g, const double* x, double* y, int mode, cudaStream_t st) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = apply_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
+  const size_t smem = table_bytes<Ops2D<T, N>>() + apply_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
   if (int rc = set_smem(apply_kernel<T, N>, smem)) return rc;
   apply_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, x, y, mode);
   CUDA_TRY(cudaGetLastError());
@@ -544,7 +544,7 @@ int record_event(std::vector<cudaEvent_t>& pool, size_t& used, cudaStream_t st) 
 template <typename T, int N>
 int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+  const size_t smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
   auto kern = cg_kernel<T, N>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
@@ -570,7 +570,8 @@ int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st
 template <int N>
 int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = mixed_smem_bytes<N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+  const size_t smem = table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>() +
+                      mixed_smem_bytes<N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
   auto kern = mixed_cg_kernel<N>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
@@ -1668,7 +1669,7 @@ size_t batch_smem_for(const dg_sim* s) {
                                                 : rhs_smem_values<double, N>(Gr.TY, Gr.TX) * sizeof(double);
     const size_t sol = s->precision == DG_FP64 ? cg_smem_bytes<double, N>(Gc.TY, Gc.TX, Lmax, pc)
                                                : mixed_smem_bytes<N>(Gc.TY, Gc.TX, Lmax, pc);
-    out = std::max(rhs, sol);
+    out = batch_ops_bytes<N>() + std::max(rhs, sol);
     return DG_OK;
   });
   return out;

@@ -14,6 +14,25 @@ namespace dgk {
 
 constexpr int kThreads = 256;
 
+// Copies an operator table (a kernel parameter or a global array) to shared memory: the
+// solves index it with per-thread node numbers, which shared memory serves without the
+// serialisation of divergent constant-bank reads.
+template <class Tab>
+__device__ __forceinline__ const Tab& stage_table(const Tab& src, unsigned char* dst) {
+  static_assert(sizeof(Tab) % 4 == 0, "table size");
+  const unsigned int* s = reinterpret_cast<const unsigned int*>(&src);
+  unsigned int* d = reinterpret_cast<unsigned int*>(dst);
+  for (int i = threadIdx.x; i < int(sizeof(Tab) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+  return *reinterpret_cast<const Tab*>(dst);
+}
+
+template <class Tab>
+__host__ __device__ constexpr size_t table_bytes() {
+  return (sizeof(Tab) + 15) & ~size_t(15);
+}
+
+
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
@@ -198,7 +217,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
                                                       const __grid_constant__ RhsArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rhs_tile<T, N>(C, G, A, blockIdx.x, smem_raw);
+  rhs_tile<T, N>(stage_table(C, smem_raw), G, A, blockIdx.x, smem_raw + table_bytes<Ops2D<T, N>>());
 }
 
 // =========================================================================================
@@ -211,12 +230,13 @@ __host__ __device__ constexpr size_t apply_smem_values(int TY, int TX) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+__global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__ Ops2D<T, N> Cp, const Geom G,
                                                         const double* __restrict__ x, double* __restrict__ y,
                                                         int mode) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sU = reinterpret_cast<T*>(smem_raw);
+  const Ops2D<T, N>& C = stage_table(Cp, smem_raw);
+  T* sU = reinterpret_cast<T*>(smem_raw + table_bytes<Ops2D<T, N>>());
   const int boxc = (G.TY + 2) * (G.TX + 2);
   T *tXR = sU + boxc * (NN + 1), *tXL = tXR + boxc * N, *tYR = tXL + boxc * N, *tYL = tYR + boxc * N;
   const TileBox B = make_box(G, blockIdx.x);
@@ -301,7 +321,7 @@ struct PrecondArgs {
   T* z;                 // cell-block part of z~ (one value per dof)
   T* rc;                // restricted residual (one per cell)
   T* uc;                // coarse correction (one per cell)
-  Cplx<T>* C;           // coarse spectrum (Ny x Nx)
+  Cplx<T>* C;           // coarse spectrum (Ny x (Nx/2 + 1))
 };
 
 // Shared memory and synchronisation of one persistent solve.
@@ -372,7 +392,8 @@ __device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& 
 }
 
 // Cell part of the preconditioner on one tile whose interior residual is staged in X.sU:
-// z~ = Bt r~ on every cell, rc = sum sqrt(W) r~ per cell; returns the tile's r~ . z~_block.
+// z~ = Bt r~ on every cell, rc = sum sqrt(W) r~ per cell (to P.rc); returns the tile's
+// r~ . z~_block.
 template <typename T, int N>
 __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const TileBox& B,
                                       const PrecondArgs<T>& P, SolveCtx<T>& X) {
@@ -397,10 +418,7 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
     T v = T(0);
 #pragma unroll
     for (int k = 0; k < NN; ++k) v = fma(C.sw[k], u[k], v);
-    const size_t cell = (size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx);
-    __stcg(P.rc + cell, v);
-    __stcg(&P.C[cell].re, v);
-    __stcg(&P.C[cell].im, T(0));
+    __stcg(P.rc + (size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx), v);
   }
   return rz;
 }
@@ -416,23 +434,40 @@ __device__ __forceinline__ void st_cplx(Cplx<T>* p, Cplx<T> v) {
   __stcg(&p->im, v.im);
 }
 
-// Coarse solve uc = A_c^+ rc from the spectrum array C (holding rc): forward DFT of the rows,
-// per column forward DFT, division by the eigenvalues, inverse DFT, then inverse DFT of the
-// rows.  Three grid-wide phases.  Returns sum uc . rc (in every block).
+// Coarse solve uc = A_c^+ rc (rc real, one value per cell).  Two real rows a, b travel as
+// one complex row a + i b: its DFT Z gives both spectra, A_k = (Z_k + conj Z_-k) / 2 and
+// B_k = (Z_k - conj Z_-k) / 2i, of which the columns kx = 0 .. Nx/2 are kept (the others are
+// their conjugates).  Then per kept column: DFT over y, division by the eigenvalues (the
+// constant mode dropped), inverse DFT; finally per row pair the inverse DFT of
+// A + i B (extended by conjugate symmetry) returns row a in the real and row b in the
+// imaginary part.  Three grid-wide phases; the spectrum array holds Ny x (Nx/2 + 1) values.
+// Returns sum uc . rc (in every block).
 template <typename T>
 __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P, SolveCtx<T>& X, T& ucrc) {
   const int Nx = G.Nx, Ny = G.Ny;
-  for (int row = X.vrank; row < Ny; row += X.vsize) {
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
+  const int Nh = Nx / 2, W = Nh + 1;  // kept columns
+  const int npairs = (Ny + 1) / 2;
+  for (int pr = X.vrank; pr < npairs; pr += X.vsize) {
+    const int ra = 2 * pr, rb = 2 * pr + 1;
+    const bool hasb = rb < Ny;
+    for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
+      const T va = __ldcg(P.rc + (size_t)ra * Nx + j);
+      const T vb = hasb ? __ldcg(P.rc + (size_t)rb * Nx + j) : T(0);
+      X.line0[dft_slot(j, P.log2x)] = Cplx<T>{va, vb};
+    }
     __syncthreads();
     dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, false);
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) st_cplx(&P.C[(size_t)row * Nx + j], X.line0[j]);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+      const Cplx<T> zk = X.line0[k], zm = X.line0[k == 0 ? 0 : Nx - k];
+      st_cplx(&P.C[(size_t)ra * W + k], Cplx<T>{T(0.5) * (zk.re + zm.re), T(0.5) * (zk.im - zm.im)});
+      if (hasb) st_cplx(&P.C[(size_t)rb * W + k], Cplx<T>{T(0.5) * (zk.im + zm.im), T(0.5) * (zm.re - zk.re)});
+    }
     __syncthreads();
   }
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
   const T scale = T(1) / (T(Nx) * T(Ny));
-  for (int col = X.vrank; col < Nx; col += X.vsize) {
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) X.line0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * Nx + col]);
+  for (int col = X.vrank; col < W; col += X.vsize) {
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) X.line0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * W + col]);
     __syncthreads();
     dft_line(X.line0, X.line1, Ny, P.log2y, P.twy, false);
     for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
@@ -442,20 +477,39 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
     }
     __syncthreads();
     dft_line(X.line1, X.line0, Ny, P.log2y, P.twy, true);
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * Nx + col], X.line1[j]);
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * W + col], X.line1[j]);
     __syncthreads();
   }
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
   T acc = T(0);
-  for (int row = X.vrank; row < Ny; row += X.vsize) {
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) X.line0[dft_slot(j, P.log2x)] = ld_cplx(&P.C[(size_t)row * Nx + j]);
+  for (int pr = X.vrank; pr < npairs; pr += X.vsize) {
+    const int ra = 2 * pr, rb = 2 * pr + 1;
+    const bool hasb = rb < Ny;
+    for (int k = threadIdx.x; k < Nx; k += blockDim.x) {
+      // A_k, B_k for k > Nx/2 are the conjugates of the kept columns Nx - k
+      const bool kept = k < W;
+      const int kk = kept ? k : Nx - k;
+      Cplx<T> A = ld_cplx(&P.C[(size_t)ra * W + kk]);
+      Cplx<T> B = hasb ? ld_cplx(&P.C[(size_t)rb * W + kk]) : Cplx<T>{T(0), T(0)};
+      if (!kept) {
+        A.im = -A.im;
+        B.im = -B.im;
+      }
+      X.line0[dft_slot(k, P.log2x)] = Cplx<T>{A.re - B.im, A.im + B.re};
+    }
     __syncthreads();
     dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, true);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
-      const size_t cell = (size_t)row * Nx + j;
-      const T u = X.line0[j].re;
-      __stcg(P.uc + cell, u);
-      acc = fma(u, __ldcg(P.rc + cell), acc);
+      const size_t ca = (size_t)ra * Nx + j;
+      const T ua = X.line0[j].re;
+      __stcg(P.uc + ca, ua);
+      acc = fma(ua, __ldcg(P.rc + ca), acc);
+      if (hasb) {
+        const size_t cb = (size_t)rb * Nx + j;
+        const T ub = X.line0[j].im;
+        __stcg(P.uc + cb, ub);
+        acc = fma(ub, __ldcg(P.rc + cb), acc);
+      }
     }
     __syncthreads();
   }
@@ -810,20 +864,21 @@ finish:
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+__global__ void __launch_bounds__(kThreads, 4) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
                                                      const __grid_constant__ CgArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[32];
   __shared__ T bcast;
   __shared__ int s_flag;
+  const Ops2D<T, N>& Cs = stage_table(C, smem_raw);
   SolveCtx<T> X;
-  init_ctx<T, N>(X, smem_raw, G, A.pc.Bt, A.precond == 1, max(G.Nx, G.Ny));
+  init_ctx<T, N>(X, smem_raw + table_bytes<Ops2D<T, N>>(), G, A.pc.Bt, A.precond == 1, max(G.Nx, G.Ny));
   X.red = red;
   X.bcast = &bcast;
   X.s_flag = &s_flag;
   X.vrank = blockIdx.x;
   X.vsize = gridDim.x;
-  cg_solve<T, N>(C, G, A, X);
+  cg_solve<T, N>(Cs, G, A, X);
 }
 
 // =========================================================================================
@@ -992,7 +1047,7 @@ finish:
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
+__global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
                                                            const __grid_constant__ Ops2D<float, N> Cf, const Geom G,
                                                            const __grid_constant__ MixedArgs A) {
   constexpr int NN = N * N;
@@ -1004,21 +1059,24 @@ __global__ void __launch_bounds__(kThreads) mixed_cg_kernel(const __grid_constan
   __shared__ int s_flag;
   const bool pc = A.precond == 1;
   const int Lmax = max(G.Nx, G.Ny);
+  const Ops2D<double, N>& Cds = stage_table(Cd, smem_raw);
+  const Ops2D<float, N>& Cfs = stage_table(Cf, smem_raw + table_bytes<Ops2D<double, N>>());
+  unsigned char* smem = smem_raw + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>();
   SolveCtx<float> Xf;
-  init_ctx<float, N>(Xf, smem_raw, G, A.pc.Bt, pc, Lmax);
+  init_ctx<float, N>(Xf, smem, G, A.pc.Bt, pc, Lmax);
   Xf.red = redf;
   Xf.bcast = &bcf;
   Xf.s_flag = &s_flag;
   Xf.vrank = blockIdx.x;
   Xf.vsize = gridDim.x;
   SolveCtx<double> Xd;
-  init_ctx<double, N>(Xd, smem_raw + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
+  init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
   Xd.red = redd;
   Xd.bcast = &bcd;
   Xd.s_flag = &s_flag;
   Xd.vrank = blockIdx.x;
   Xd.vsize = gridDim.x;
-  mixed_solve<N>(Cd, Cf, G, A, Xf, Xd);
+  mixed_solve<N>(Cds, Cfs, G, A, Xf, Xd);
 }
 
 // =========================================================================================
@@ -1089,14 +1147,23 @@ __device__ __forceinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& 
 
 // One AB3 step of simulation S on a group.  Returns false after a barrier timeout.
 template <int N>
-__device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int vrank, unsigned char* smem,
+__host__ __device__ constexpr size_t batch_ops_bytes() {
+  return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>();
+}
+
+template <int N>
+__device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int vrank, unsigned char* smem_all,
                                            double* redd, double* bcd, float* redf, float* bcf, int* s_flag) {
   constexpr int NN = N * N;
   const BatchSim& S = *Sp;
   const int oc = __ldcg(&Sp->oc), p0 = __ldcg(&Sp->p0), p1 = __ldcg(&Sp->p1), p2 = __ldcg(&Sp->p2);
   const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), r3 = __ldcg(&Sp->r3), rfree = __ldcg(&Sp->rfree);
-  const Ops2D<double, N>& Cd = *static_cast<const Ops2D<double, N>*>(S.ops_d);
-  const Ops2D<float, N>& Cf = *static_cast<const Ops2D<float, N>*>(S.ops_f);
+  // this simulation's operator tables, staged in shared memory (the previous step's last
+  // barrier has synchronised the block)
+  const Ops2D<double, N>& Cd = stage_table(*static_cast<const Ops2D<double, N>*>(S.ops_d), smem_all);
+  const Ops2D<float, N>& Cf =
+      stage_table(*static_cast<const Ops2D<float, N>*>(S.ops_f), smem_all + table_bytes<Ops2D<double, N>>());
+  unsigned char* smem = smem_all + batch_ops_bytes<N>();
   if (S.precision == 1)
     batch_rhs<float, N>(S, Cf, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
   else

@@ -51,13 +51,14 @@ def translated_dipole(X, Y, t, U=1.0):
     return fields.lamb_dipole(X, yc + dy, xc=0.5, yc=yc)
 
 
-def dipole_shape(dg, N, n, bracket, t_end=0.5, U_bound=4.0):
-    """Runs the dipole to t_end; returns a dict of the shape error and invariant drifts."""
+def dipole_shape(dg, N, n, bracket, t_end=0.5, U_bound=4.0, tol=1e-11):
+    """Runs the dipole to t_end (CG tolerance tol); returns a dict of the shape error and the
+    invariant drifts."""
     import torch
     dt = workloads.stable_dt(dg, N, n, 0.0, L=1.0, U=U_bound, dt_cap=1e-3)
     steps = int(np.ceil(t_end / dt))
     dt = t_end / steps
-    g, sim, X, Y = lamb_sim(dg, N, n, dt, K=3, bracket=bracket)
+    g, sim, X, Y = lamb_sim(dg, N, n, dt, K=3, bracket=bracket, tol=tol)
     V0, E0, O0 = sim.invariants()
     sim.step(steps)
     V, E, O = sim.invariants()

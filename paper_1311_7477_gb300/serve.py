@@ -2,9 +2,9 @@
 
 Requests (cells per side N, nodes n, viscosity D, number of steps, initial field) arrive
 over time.  A request is admitted as soon as a batch slot is free and its device-memory
-footprint fits the HBM budget; admission builds its grid and simulation (initial Poisson
-solve) and takes its two RK4 start-up steps, then the request joins the batch
-(dg_batch_admit).  The GPU loop advances every admitted simulation with one persistent,
+footprint fits the HBM budget; admission builds its simulation (initial Poisson solve) on a
+grid shared by all requests of the same (N, n) and takes its two RK4 start-up steps, then
+the request joins the batch (dg_batch_admit).  The GPU loop advances every admitted simulation with one persistent,
 graph-captured launch per chunk of steps (dg_batch_step); a simulation that has taken all its
 steps is retired, its latency (arrival -> completion) recorded and its memory freed, which
 admits waiting requests.  Requests that arrive while others are on the GPU therefore overlap
@@ -62,16 +62,28 @@ class Server:
         self.done = []
         self.results = {}
         self.dof_steps = 0
+        self.grids = {}           # (N, n) -> dg.Grid, shared by the requests of that shape
+        self.t = {"field": 0.0, "create": 0.0, "admit": 0.0, "step": 0.0, "finish": 0.0}
 
-    def _admit(self, req, now):
+    def _grid(self, N, n):
+        g = self.grids.get((N, n))
+        if g is None:
+            g = dg.Grid(N, N, n)
+            g.set_precond(self.precond)
+            self.grids[(N, n)] = g
+        return g
+
+    def _admit(self, req, now, clock):
         import torch
         s = req.spec
-        g = dg.Grid(s["N"], s["N"], s["n"])
-        g.set_precond(self.precond)
+        t0 = clock()
+        g = self._grid(s["N"], s["n"])
         w0 = torch.from_numpy(workloads.initial_field(dg, g, s)).cuda()
+        t1 = clock()
         dt = workloads.stable_dt(dg, s["N"], s["n"], s["D"], dt_cap=self.dt_cap)
         sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=self.precision, cg_tol=self.cg_tol, cg_maxit=100000)
         del w0
+        t2 = clock()
         req.grid, req.sim = g, sim
         req.admit_t = now
         steps0 = min(2, req.steps)
@@ -81,12 +93,17 @@ class Server:
         else:
             self.batch.admit(sim)          # the two RK4 start-up steps run here
             req.remaining = req.steps - 2
+        t3 = clock()
+        self.t["field"] += t1 - t0
+        self.t["create"] += t2 - t1
+        self.t["admit"] += t3 - t2
         self.dof_steps += req.dof * steps0
         self.used += footprint(s["N"], s["n"], self.precision)
         self.active.append(req)
 
-    def _finish(self, req, now):
+    def _finish(self, req, now, clock=time.perf_counter):
         import torch
+        t0 = clock()
         if req.sim in self.batch.members:
             self.batch.retire(req.sim)
         torch.cuda.synchronize()
@@ -98,11 +115,11 @@ class Server:
             torch.cuda.synchronize()
             self.results[req.id] = (om.cpu().numpy(), ps.cpu().numpy(), req.sim.status().step)
         req.sim.close()
-        req.grid.close()
         req.sim = req.grid = None
         self.used -= footprint(req.spec["N"], req.spec["n"], self.precision)
         self.active.remove(req)
         self.done.append(req)
+        self.t["finish"] += clock() - t0
 
     def run(self, trace, time_scale=1.0, clock=time.perf_counter):
         """Serves the trace (arrival times scaled by time_scale); returns the report dict."""
@@ -122,16 +139,18 @@ class Server:
                 if self.used + need > self.budget and self.active:
                     break
                 queue.pop(0)
-                self._admit(r, clock() - t0)
+                self._admit(r, clock() - t0, clock)
             for r in [r for r in self.active if r.remaining == 0]:
-                self._finish(r, clock() - t0)
+                self._finish(r, clock() - t0, clock)
             runnable = [r for r in self.active if r.remaining > 0]
             if not runnable:
                 if pending and not queue:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival * time_scale - (clock() - t0))))
                 continue
             k = min(self.chunk, min(r.remaining for r in runnable))
+            ts = clock()
             self.batch.step(k)
+            self.t["step"] += clock() - ts
             launches += 1
             for r in runnable:
                 r.remaining -= k
@@ -140,7 +159,7 @@ class Server:
             if finished:
                 torch.cuda.synchronize()
                 for r in finished:
-                    self._finish(r, clock() - t0)
+                    self._finish(r, clock() - t0, clock)
         torch.cuda.synchronize()
         wall = clock() - t0
         lat = np.array([r.done_t - r.arrival * time_scale for r in self.done])
@@ -149,4 +168,10 @@ class Server:
                 "mdof_steps_per_s": self.dof_steps / wall / 1e6,
                 "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
-                "batch_launches": launches, "batch_status": st["rc"], "graph": st["graph"]}
+                "batch_launches": launches, "batch_status": st["rc"], "graph": st["graph"],
+                "host_seconds": dict(self.t), "grids": len(self.grids)}
+
+    def close(self):
+        for g in self.grids.values():
+            g.close()
+        self.grids = {}
