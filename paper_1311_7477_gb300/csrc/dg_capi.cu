@@ -1589,6 +1589,7 @@ struct dg_batch {
   std::vector<dg_sim*> sims;
   int ngroups_req = 0;  // 0: automatic
   bool dirty = true;    // composition or plan changed: re-plan, re-upload, re-capture
+  int stable = 0;       // launches since the last re-plan
   BatchSim* d_sims = nullptr;
   int* d_order = nullptr;
   BatchGroup* d_groups = nullptr;
@@ -1604,6 +1605,12 @@ struct dg_batch {
   bool use_graph = true;
   char graph_error[256] = "";
   long long launches = 0;
+  // pinned staging of the plan (uploaded asynchronously on the step's stream)
+  BatchSim* h_sims = nullptr;
+  int* h_order = nullptr;
+  BatchGroup* h_groups = nullptr;
+  cudaEvent_t ev_upload = nullptr;
+  bool upload_pending = false;
 };
 
 namespace {
@@ -1677,7 +1684,7 @@ size_t batch_smem_for(const dg_sim* s) {
 
 // Splits the simulations into groups of balanced work (longest processing time first; work
 // ~ dof) and the co-resident blocks among the groups in proportion to their work.
-int batch_plan(dg_batch* b, int dev_sms) {
+int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
   const int ns = (int)b->sims.size();
   size_t smem = 0;
   for (dg_sim* s : b->sims) smem = std::max(smem, batch_smem_for(s));
@@ -1727,11 +1734,16 @@ int batch_plan(dg_batch* b, int dev_sms) {
     for (int i : members[k]) b->order.push_back(i);
     fb += nb[k];
   }
-  std::vector<BatchSim> hs(ns);
-  for (int i = 0; i < ns; ++i) hs[i] = make_batch_sim(b->sims[i]);
-  CUDA_TRY(cudaMemcpy(b->d_sims, hs.data(), ns * sizeof(BatchSim), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(b->d_order, b->order.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(b->d_groups, b->groups.data(), G * sizeof(BatchGroup), cudaMemcpyHostToDevice));
+  // the staging buffers are rewritten only after the previous upload has executed
+  if (b->upload_pending) CUDA_TRY(cudaEventSynchronize(b->ev_upload));
+  for (int i = 0; i < ns; ++i) b->h_sims[i] = make_batch_sim(b->sims[i]);
+  std::copy(b->order.begin(), b->order.end(), b->h_order);
+  std::copy(b->groups.begin(), b->groups.end(), b->h_groups);
+  CUDA_TRY(cudaMemcpyAsync(b->d_sims, b->h_sims, ns * sizeof(BatchSim), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(b->d_order, b->h_order, ns * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(b->d_groups, b->h_groups, G * sizeof(BatchGroup), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaEventRecord(b->ev_upload, st));
+  b->upload_pending = true;
   b->grid = grid;
   b->ngroups = G;
   b->smem = smem;
@@ -1740,6 +1752,7 @@ int batch_plan(dg_batch* b, int dev_sms) {
     b->graph = nullptr;
   }
   b->dirty = false;
+  b->stable = 0;
   return DG_OK;
 }
 
@@ -1793,6 +1806,10 @@ int dg_batch_create(dg_batch** bp, int max_sims) {
     CUDA_TRY(cudaMalloc(&b->d_sync, b->cap_groups * sizeof(SyncState)));
     CUDA_TRY(cudaMalloc(&b->d_error, sizeof(int)));
     CUDA_TRY(cudaMemset(b->d_error, 0, sizeof(int)));
+    CUDA_TRY(cudaMallocHost(&b->h_sims, max_sims * sizeof(BatchSim)));
+    CUDA_TRY(cudaMallocHost(&b->h_order, max_sims * sizeof(int)));
+    CUDA_TRY(cudaMallocHost(&b->h_groups, b->cap_groups * sizeof(BatchGroup)));
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming));
     return DG_OK;
   };
   if (int rc = alloc()) {
@@ -1811,6 +1828,10 @@ int dg_batch_destroy(dg_batch* b) {
   cudaFree(b->d_groups);
   cudaFree(b->d_sync);
   cudaFree(b->d_error);
+  if (b->h_sims) cudaFreeHost(b->h_sims);
+  if (b->h_order) cudaFreeHost(b->h_order);
+  if (b->h_groups) cudaFreeHost(b->h_groups);
+  if (b->ev_upload) cudaEventDestroy(b->ev_upload);
   delete b;
   return DG_OK;
 }
@@ -1857,8 +1878,10 @@ int dg_batch_step(dg_batch* b, int nsteps, void* stream) {
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (b->dirty)
-    if (int rc = batch_plan(b, sms)) return rc;
-  if (b->use_graph && (!b->graph || b->graph_steps != nsteps)) {
+    if (int rc = batch_plan(b, sms, st)) return rc;
+  // a CUDA graph once the plan has served two launches unchanged (a batch whose members
+  // change at every launch, as under continuous batching, launches directly)
+  if (b->use_graph && b->stable >= 2 && (!b->graph || b->graph_steps != nsteps)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -1888,6 +1911,7 @@ int dg_batch_step(dg_batch* b, int nsteps, void* stream) {
     return rc;
   }
   b->launches += 1;
+  b->stable += 1;
   batch_advance_host(b, nsteps);
   return DG_OK;
 }

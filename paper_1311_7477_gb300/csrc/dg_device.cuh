@@ -181,8 +181,8 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return t;
 }
 
-// Sum of G per-block partials p[i*stride], in a fixed order, returned to every thread.
-// Every block computes the bit-identical value.  Reads bypass L1 (written by other blocks).
+// Sum of G per-block partials p[i*stride], in a fixed order, returned to every thread of a
+// one-warp launch.  Reads bypass L1 (written by other blocks).
 template <typename T>
 __device__ __forceinline__ T sum_partials(const T* p, int G, int stride, T* bcast) {
   if (threadIdx.x < 32) {
@@ -191,6 +191,21 @@ __device__ __forceinline__ T sum_partials(const T* p, int G, int stride, T* bcas
     v = warp_sum_down(v);
     if (threadIdx.x == 0) *bcast = v;
   }
+  __syncthreads();
+  const T r = *bcast;
+  __syncthreads();
+  return r;
+}
+
+// The same with the whole block: thread t adds the partials t, t + blockDim.x, ... in
+// order, then a fixed-shape block reduction.  Every block computes the bit-identical value
+// (the order depends only on G and blockDim.x); one round of loads instead of G / 32.
+template <typename T>
+__device__ __forceinline__ T sum_partials_block(const T* p, int G, int stride, T* red, T* bcast) {
+  T v = T(0);
+  for (int i = threadIdx.x; i < G; i += blockDim.x) v += __ldcg(p + (size_t)i * stride);
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) *bcast = v;
   __syncthreads();
   const T r = *bcast;
   __syncthreads();

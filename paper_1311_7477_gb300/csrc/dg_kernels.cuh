@@ -348,7 +348,7 @@ __device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
   v0 = block_sum(v0, X.red);
   if (threadIdx.x == 0) __stcg(ph + X.vrank, v0);
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
-  out0 = sum_partials(ph, X.vsize, 1, X.bcast);
+  out0 = sum_partials_block(ph, X.vsize, 1, X.red, X.bcast);
   return true;
 }
 
@@ -361,8 +361,8 @@ __device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0,
   v1 = block_sum(v1, X.red);
   if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank + 1, v1);
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
-  out0 = sum_partials(ph, X.vsize, 2, X.bcast);
-  out1 = sum_partials(ph + 1, X.vsize, 2, X.bcast);
+  out0 = sum_partials_block(ph, X.vsize, 2, X.red, X.bcast);
+  out1 = sum_partials_block(ph + 1, X.vsize, 2, X.red, X.bcast);
   return true;
 }
 

@@ -1,7 +1,8 @@
 """Continuous-batching simulation server on one GPU.
 
-Requests (cells per side N, nodes n, viscosity D, number of steps, initial field) arrive
-over time.  A request is admitted as soon as a batch slot is free and its device-memory
+Requests (cells per side N, nodes n, viscosity D, number of steps, initial field -- given
+as node values in "omega0", or generated from the spec's field recipe by host threads)
+arrive over time.  A request is admitted as soon as a batch slot is free and its device-memory
 footprint fits the HBM budget; admission builds its simulation (initial Poisson solve) on a
 grid shared by all requests of the same (N, n) and takes its two RK4 start-up steps, then
 the request joins the batch (dg_batch_admit).  The GPU loop advances every admitted simulation with one persistent,
@@ -39,6 +40,8 @@ class Request:
         self.grid = None
         self.sim = None
         self.remaining = None
+        self.field = None
+        self.closing = False
 
     @property
     def dof(self):
@@ -73,12 +76,32 @@ class Server:
             self.grids[(N, n)] = g
         return g
 
+    def _field(self, spec):
+        """Host-side initial field of a request (runs in the prefetch threads)."""
+        xn, yn = self.nodes[(spec["N"], spec["n"])]
+        return workloads.initial_field_from_nodes(xn, yn, spec)
+
+    def _prefetch(self, req):
+        s = req.spec
+        if s.get("omega0") is not None:        # the request carries its initial field
+            from concurrent.futures import Future
+            req.field = Future()
+            req.field.set_result(s["omega0"])
+            return
+        key = (s["N"], s["n"])
+        if key not in self.nodes:
+            g = self._grid(*key)
+            xn, yn, _ = g.nodes()
+            self.nodes[key] = (xn, yn)
+        req.field = self.pool.submit(self._field, s)
+
     def _admit(self, req, now, clock):
         import torch
         s = req.spec
         t0 = clock()
         g = self._grid(s["N"], s["n"])
-        w0 = torch.from_numpy(workloads.initial_field(dg, g, s)).cuda()
+        w0 = torch.from_numpy(req.field.result()).cuda()
+        req.field = None
         t1 = clock()
         dt = workloads.stable_dt(dg, s["N"], s["n"], s["D"], dt_cap=self.dt_cap)
         sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=self.precision, cg_tol=self.cg_tol, cg_maxit=100000)
@@ -102,11 +125,10 @@ class Server:
         self.active.append(req)
 
     def _finish(self, req, now, clock=time.perf_counter):
+        """The request's last step has completed on the device: record it, keep its result if
+        asked, and free its memory (deferred: a free would wait for the running step)."""
         import torch
         t0 = clock()
-        if req.sim in self.batch.members:
-            self.batch.retire(req.sim)
-        torch.cuda.synchronize()
         req.done_t = now
         if self.keep_results:
             om = torch.empty(req.grid.shape, dtype=torch.float64, device="cuda")
@@ -114,53 +136,98 @@ class Server:
             req.sim.get(om, ps)
             torch.cuda.synchronize()
             self.results[req.id] = (om.cpu().numpy(), ps.cpu().numpy(), req.sim.status().step)
-        req.sim.close()
+        self.graveyard.append(req.sim)
         req.sim = req.grid = None
         self.used -= footprint(req.spec["N"], req.spec["n"], self.precision)
         self.active.remove(req)
         self.done.append(req)
         self.t["finish"] += clock() - t0
 
+    def _bury(self):
+        for sim in self.graveyard:
+            sim.close()
+        self.graveyard = []
+
     def run(self, trace, time_scale=1.0, clock=time.perf_counter):
-        """Serves the trace (arrival times scaled by time_scale); returns the report dict."""
+        """Serves the trace (arrival times scaled by time_scale); returns the report dict.
+
+        One loop: arrivals join the queue and their initial fields are generated by host
+        threads; the next batched step is launched as soon as the previous one has been
+        queued, so that admissions (host work, then the new simulation's start-up solves on
+        the device) overlap the running step; a request whose last step was launched leaves
+        the batch at once and completes when that launch's event has fired."""
         import torch
+        from concurrent.futures import ThreadPoolExecutor
         pending = sorted((Request(s) for s in trace), key=lambda r: r.arrival)
         queue = []
+        inflight = []          # (event, requests whose last step is in that launch)
+        self.graveyard = []
+        self.nodes = {}
+        self.pool = ThreadPoolExecutor(max_workers=4)
         t0 = clock()
         launches = 0
-        while pending or queue or self.active:
-            now = clock() - t0
-            while pending and pending[0].arrival * time_scale <= now:
-                queue.append(pending.pop(0))
-            # admission by free slots and by the HBM budget (FIFO)
-            while queue and len(self.active) < self.max_active:
-                r = queue[0]
-                need = footprint(r.spec["N"], r.spec["n"], self.precision)
-                if self.used + need > self.budget and self.active:
-                    break
-                queue.pop(0)
-                self._admit(r, clock() - t0, clock)
-            for r in [r for r in self.active if r.remaining == 0]:
-                self._finish(r, clock() - t0, clock)
-            runnable = [r for r in self.active if r.remaining > 0]
-            if not runnable:
-                if pending and not queue:
-                    time.sleep(max(0.0, min(0.01, pending[0].arrival * time_scale - (clock() - t0))))
-                continue
-            k = min(self.chunk, min(r.remaining for r in runnable))
-            ts = clock()
-            self.batch.step(k)
-            self.t["step"] += clock() - ts
-            launches += 1
-            for r in runnable:
-                r.remaining -= k
-                self.dof_steps += r.dof * k
-            finished = [r for r in runnable if r.remaining == 0]
-            if finished:
-                torch.cuda.synchronize()
-                for r in finished:
-                    self._finish(r, clock() - t0, clock)
-        torch.cuda.synchronize()
+        try:
+            while pending or queue or self.active:
+                now = clock() - t0
+                while pending and pending[0].arrival * time_scale <= now:
+                    r = pending.pop(0)
+                    self._prefetch(r)
+                    queue.append(r)
+                # completions
+                still = []
+                for ev, reqs in inflight:
+                    if ev.query():
+                        for r in reqs:
+                            self._finish(r, clock() - t0, clock)
+                    else:
+                        still.append((ev, reqs))
+                inflight = still
+                # admissions by free slots and the HBM budget (FIFO); their host work overlaps
+                # the step in flight
+                admitted = False
+                while queue and len(self.active) < self.max_active:
+                    r = queue[0]
+                    need = footprint(r.spec["N"], r.spec["n"], self.precision)
+                    if self.used + need > self.budget and self.active:
+                        break
+                    queue.pop(0)
+                    self._admit(r, clock() - t0, clock)
+                    admitted = True
+                if self.graveyard and admitted:
+                    self._bury()   # the admission has synchronised the device: frees do not stall
+                # requests with no steps left leave the batch before the next launch; they
+                # complete with the work queued so far
+                done_now = [r for r in self.active if r.remaining == 0 and not r.closing]
+                if done_now:
+                    for r in done_now:
+                        r.closing = True
+                        if r.sim in self.batch.members:
+                            self.batch.retire(r.sim)
+                    ev = torch.cuda.Event()
+                    ev.record()
+                    inflight.append((ev, done_now))
+                # the next batched step, for every member with steps left
+                runnable = [r for r in self.active if r.remaining > 0]
+                if runnable:
+                    k = min(self.chunk, min(r.remaining for r in runnable))
+                    ts = clock()
+                    self.batch.step(k)
+                    self.t["step"] += clock() - ts
+                    launches += 1
+                    for r in runnable:
+                        r.remaining -= k
+                        self.dof_steps += r.dof * k
+                if not runnable and not admitted:
+                    if inflight:
+                        inflight[0][0].synchronize()
+                    elif self.graveyard:
+                        self._bury()
+                    elif pending and not queue:
+                        time.sleep(max(0.0, min(0.01, pending[0].arrival * time_scale - (clock() - t0))))
+            torch.cuda.synchronize()
+            self._bury()
+        finally:
+            self.pool.shutdown(wait=True)
         wall = clock() - t0
         lat = np.array([r.done_t - r.arrival * time_scale for r in self.done])
         st = self.batch.status(check=False)

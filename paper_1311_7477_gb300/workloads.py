@@ -74,8 +74,12 @@ def request_trace(count=200, rate=20.0, seed=7, Ns=(64, 128, 256, 512, 1024), ns
 
 
 def initial_field(dg, grid, spec):
-    from . import fields
     xn, yn, _ = grid.nodes()
+    return initial_field_from_nodes(xn, yn, spec)
+
+
+def initial_field_from_nodes(xn, yn, spec):
+    from . import fields
     X, Y = fields.mesh_from_nodes(xn, yn)
     if spec["field"] == "random_phase":
         return fields.random_phase(X, Y, seed=spec["seed"])
