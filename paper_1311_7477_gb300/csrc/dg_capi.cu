@@ -139,6 +139,27 @@ void default_tiles(int n, int& rty, int& rtx, int& cty, int& ctx) {
   ctx = Cg[n][1];
 }
 
+// Small grids: halve the larger tile side until the grid has at least one tile per SM (or
+// the tile is down to 4 cells), so that the few cells are spread over many blocks -- the
+// solves' phases are then short chains of work rather than long loops in a few blocks.
+void fit_tile(int Nx, int Ny, int sms, int& ty, int& tx) {
+  auto tiles = [&]() { return (long long)((Nx + tx - 1) / tx) * ((Ny + ty - 1) / ty); };
+  while (tiles() < sms && ty * tx > 4) {
+    if (tx >= ty && tx > 1)
+      tx /= 2;
+    else if (ty > 1)
+      ty /= 2;
+    else
+      break;
+  }
+}
+
+void choose_tiles(int n, int Nx, int Ny, int sms, int& rty, int& rtx, int& cty, int& ctx) {
+  default_tiles(n, rty, rtx, cty, ctx);
+  fit_tile(Nx, Ny, sms, rty, rtx);
+  fit_tile(Nx, Ny, sms, cty, ctx);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -706,7 +727,6 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
   g->hy = Ly / Ny;
   g->tau = tau;
   build_ref_tables(n, tau, &g->rt);
-  default_tiles(n, g->rTY, g->rTX, g->cTY, g->cTX);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -714,6 +734,7 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
     delete g;
     return fail(DG_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
   }
+  choose_tiles(n, Nx, Ny, g->num_sms, g->rTY, g->rTX, g->cTY, g->cTX);
   dispatch_n(n, [&](auto nc) {
     build_ops<decltype(nc)::value>(g);
     return DG_OK;
@@ -769,7 +790,7 @@ int dg_grid_nodes(const dg_grid* g, double* xn, double* yn, double* w) {
 int dg_grid_set_tiles(dg_grid* g, int TY, int TX) {
   if (!g) return fail(DG_ERR_ARG, "g is NULL");
   if (TY == 0 && TX == 0) {
-    default_tiles(g->n, g->rTY, g->rTX, g->cTY, g->cTX);
+    choose_tiles(g->n, g->Nx, g->Ny, g->num_sms, g->rTY, g->rTX, g->cTY, g->cTX);
     return DG_OK;
   }
   if (TY < 1 || TX < 1 || TY > 64 || TX > 64) return fail(DG_ERR_ARG, "tile must be 1..64 cells per side");
@@ -1538,10 +1559,10 @@ extern "C" int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double 
   g.hy = Ly / Ny;
   g.tau = tau;
   build_ref_tables(n, tau, &g.rt);
-  default_tiles(n, g.rTY, g.rTX, g.cTY, g.cTX);
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  choose_tiles(n, Nx, Ny, g.num_sms, g.rTY, g.rTX, g.cTY, g.cTX);
   dispatch_n(n, [&](auto nc) {
     build_ops<decltype(nc)::value>(&g);
     return DG_OK;
@@ -1615,14 +1636,22 @@ struct dg_batch {
 
 namespace {
 
+// Tiles of a simulation inside a batch: the built-in ones for its n (a small grid's blocks
+// are few in a batch group, so its tiles are not split further as for a whole-GPU solve).
+void batch_geoms(const dg_grid* g, Geom* Gr, Geom* Gc) {
+  int rty, rtx, cty, ctx;
+  default_tiles(g->n, rty, rtx, cty, ctx);
+  *Gr = geom_of(g, rty, rtx);
+  *Gc = geom_of(g, cty, ctx);
+}
+
 BatchSim make_batch_sim(dg_sim* s) {
   dg_grid* g = s->g;
   BatchSim b{};
   b.n = g->n;
   b.precision = s->precision == DG_FP64 ? 0 : (s->precision == DG_MIXED ? 1 : 2);
   b.precond = g->precond;
-  b.Gr = geom_of(g, g->rTY, g->rTX);
-  b.Gc = geom_of(g, g->cTY, g->cTX);
+  batch_geoms(g, &b.Gr, &b.Gc);
   b.ops_d = g->d_opsd;
   b.ops_f = g->d_opsf;
   for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
@@ -1666,7 +1695,8 @@ BatchSim make_batch_sim(dg_sim* s) {
 // Dynamic shared memory one simulation needs in batch_kernel (RHS tile and solve share it).
 size_t batch_smem_for(const dg_sim* s) {
   const dg_grid* g = s->g;
-  const Geom Gr = geom_of(g, g->rTY, g->rTX), Gc = geom_of(g, g->cTY, g->cTX);
+  Geom Gr, Gc;
+  batch_geoms(g, &Gr, &Gc);
   const int Lmax = std::max(g->Nx, g->Ny);
   const bool pc = g->precond == DG_PRECOND_TWOLEVEL;
   size_t out = 0;

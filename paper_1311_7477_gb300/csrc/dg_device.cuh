@@ -69,19 +69,22 @@ __device__ __forceinline__ void stage_box(const Geom& G, const TileBox& B, T* sU
   constexpr int NN = N * N;
   const int BWe = B.TXe + 2, BHe = B.TYe + 2;
   const int rowlen = BWe * NN;
-  for (int br = 0; br < BHe; ++br) {
+  const int total = BHe * rowlen;
+  // one flat loop over the whole box, so that a thread's loads of several rows are in flight
+  // together
+#pragma unroll 4
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int br = i / rowlen;
+    const int j = i - br * rowlen;
+    const int bc = j / NN;
+    const int k = j - bc * NN;
     const bool rowhalo = (br == 0) || (br == BHe - 1);
+    const bool colhalo = (bc == 0) || (bc == BWe - 1);
+    if (rowhalo && colhalo && !corners) continue;
     const int cy = wrap_index(B.ty0 + br - 1, G.Ny);
-    const size_t rowbase = (size_t)cy * G.Nx;
-    for (int j = threadIdx.x; j < rowlen; j += blockDim.x) {
-      const int bc = j / NN;
-      const int k = j - bc * NN;
-      const bool colhalo = (bc == 0) || (bc == BWe - 1);
-      if (rowhalo && colhalo && !corners) continue;
-      const int cx = wrap_index(B.tx0 + bc - 1, G.Nx);
-      const size_t g = (rowbase + cx) * NN + k;
-      sU[(br * B.BW + bc) * (NN + 1) + k] = load(g, k, !(rowhalo || colhalo));
-    }
+    const int cx = wrap_index(B.tx0 + bc - 1, G.Nx);
+    const size_t g = ((size_t)cy * G.Nx + cx) * NN + k;
+    sU[(br * B.BW + bc) * (NN + 1) + k] = load(g, k, !(rowhalo || colhalo));
   }
 }
 
