@@ -111,7 +111,9 @@ int dg_grid_nodes(const dg_grid* g, double* x_nodes, double* y_nodes, double* we
 
 /*
  * dg_grid_set_tiles -- override the kernels' cell tile (TY x TX cells per thread block);
- * 0 restores the built-in choice for this n.  Used by the autotuner.  Errors: DG_ERR_ARG.
+ * 0 restores the built-in choice for this n (tiles halved on small grids until there is
+ * about one per SM).  Batched simulations use the built-in tiles.  Used by the autotuner.
+ * Errors: DG_ERR_ARG.
  */
 int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
 
@@ -292,9 +294,10 @@ int dg_sim_invariants(dg_sim* s, double out[3], void* stream);
 int dg_sim_set_cg(dg_sim* s, double tol, int maxit, int fixed_iters);
 
 /*
- * dg_sim_set_refinement -- DG_MIXED only: each float32 inner CG sweep stops when its residual
- * has fallen by tol_in (0 < tol_in < 1); at most max_sweeps >= 1 float64 refinement sweeps per
- * solve (the float64 residual must reach the CG tolerance of dg_sim_create / dg_sim_set_cg).
+ * dg_sim_set_refinement -- DG_MIXED / DG_MIXED64: each float32 inner CG sweep stops when its
+ * residual has fallen by tol_in (0 < tol_in < 1), or by half the factor still missing to the
+ * CG tolerance if that is looser; at most max_sweeps >= 1 float64 refinement sweeps per solve
+ * (the float64 residual must reach the CG tolerance of dg_sim_create / dg_sim_set_cg).
  */
 int dg_sim_set_refinement(dg_sim* s, double tol_in, int max_sweeps);
 

@@ -1000,7 +1000,10 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
       flags |= kFlagNoconv;
       break;
     }
-    // float32 inner (P)CG from e = 0 on the residual equation
+    // float32 inner (P)CG from e = 0 on the residual equation, to the relative tolerance
+    // tol_in -- or to what is left to reach the outer tolerance (with a factor 1/2 of
+    // margin), if that is looser: the last sweep then does only the iterations it needs
+    const double tol_eff2 = fmax(A.tol_in2, 0.25 * A.tol2 * bb / rr);
     float rho_in = float(rr);
     const float rhob_in = rho_in;
     float rz_in = rho_in;
@@ -1010,7 +1013,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
     }
     int fin = 0;
     const int it_in = cg_iterate<float, N>(Cf, G, A.v, pc ? &A.pc : nullptr, RhsSource<float>{nullptr, A.rf, 0.0f},
-                                           Xf, rho_in, rz_in, rhob_in, A.tol_in2, A.maxit_in, 0, fin, 0);
+                                           Xf, rho_in, rz_in, rhob_in, tol_eff2, A.maxit_in, 0, fin, 0);
     inner += it_in;
     if (fin & kFlagTimeout) {
       flags |= kFlagTimeout;
