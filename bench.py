@@ -301,7 +301,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64", "fp64pc32"])
     ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel"])
     ap.add_argument("--no-mixed-compare", action="store_true")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -343,7 +343,7 @@ def main():
     _build.build()
     from paper_1311_7477_gb300 import dg, fields
 
-    precision = {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED, "mixed64": dg.DG_MIXED64}[args.precision]
+    precision = _prec(dg, args.precision)
     N, n = wl["N"], wl["n"]
     g = dg.Grid(N, N, n)
     g.set_precond(args.precond)
@@ -440,7 +440,7 @@ def main():
         ref_w, ref_p = torch.empty_like(st[0]), torch.empty_like(st[0])
         sim.step(1)
         sim.get(ref_w, ref_p)
-        for mname, mprec in (("mixed64", dg.DG_MIXED64), ("mixed", dg.DG_MIXED)):
+        for mname, mprec in (("fp64pc32", dg.DG_FP64_PC32), ("mixed64", dg.DG_MIXED64), ("mixed", dg.DG_MIXED)):
             ms_ = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=mprec, cg_tol=wl["tol"], cg_maxit=200000)
             ms_.set_state(kk, *st)
             ms_.step(1)
@@ -464,7 +464,9 @@ def main():
                             "inner_cg_iters_per_step": (info.cg_iters_total - i0) / args.steps,
                             "refine_sweeps_last": int(info.refine_sweeps_last),
                             "error_vs_fp64_one_step": err,
-                            "what": {"mixed64": "float64 bracket/viscous term/update, float32 inner CG, "
+                            "what": {"fp64pc32": "float64 throughout except the CG preconditioner (cell block "
+                                                 "solve and coarse DFT solve), applied in float32",
+                                     "mixed64": "float64 bracket/viscous term/update, float32 inner CG, "
                                                 "float64 refinement residual",
                                      "mixed": "float32 bracket and inner CG, float64 update and refinement"}[mname]}
             ms_.close()
@@ -641,7 +643,7 @@ def run_bracket(args):
 
 
 def _prec(dg, name):
-    return {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED, "mixed64": dg.DG_MIXED64}[name]
+    return {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED, "mixed64": dg.DG_MIXED64, "fp64pc32": dg.DG_FP64_PC32}[name]
 
 
 def run_batch(args):

@@ -56,6 +56,8 @@ extern "C" {
 #define DG_FP64 0     /* everything in float64                                             */
 #define DG_MIXED 1    /* bracket and inner CG in float32, float64 refinement, state and sums */
 #define DG_MIXED64 2  /* bracket in float64, inner CG in float32, float64 refinement, state  */
+#define DG_FP64_PC32 3 /* float64 everywhere except the CG preconditioner, applied in float32 */
+                       /* (a float32 copy of the cell block solve and the coarse DFT solve)   */
 
 typedef struct dg_grid dg_grid;
 typedef struct dg_sim dg_sim;

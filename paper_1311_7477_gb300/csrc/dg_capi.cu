@@ -562,11 +562,11 @@ int record_event(std::vector<cudaEvent_t>& pool, size_t& used, cudaStream_t st) 
   return DG_OK;
 }
 
-template <typename T, int N>
-int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
+template <typename T, int N, typename TP = T>
+int launch_cg(const dg_grid* g, CgArgs<T, TP> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
   const Geom G = geom_of(g, g->cTY, g->cTX);
   const size_t smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
-  auto kern = cg_kernel<T, N>;
+  auto kern = cg_kernel<T, N, TP>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
@@ -576,7 +576,10 @@ int launch_cg(const dg_grid* g, CgArgs<T> A, const Workspace& w, cudaStream_t st
   A.part = reinterpret_cast<T*>(w.part);
   A.sync = w.sync;
   A.status = w.status;
-  if constexpr (sizeof(T) == 8) A.pc = pc_args(g, w);
+  if constexpr (std::is_same<TP, double>::value)
+    A.pc = pc_args(g, w);
+  else
+    A.pc = pc_args_f(g, w);
   CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
   void* args[] = {(void*)&ops_of<T, N>(g), (void*)&G, (void*)&A};
   const bool tm = timed && timed->timing;
@@ -911,7 +914,22 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
               cudaStream_t st) {
   dg_grid* g = s->g;
   int rc;
-  if (s->precision != DG_FP64) {
+  if (s->precision == DG_FP64_PC32) {
+    CgArgs<double, float> A{};
+    A.omega = omega;
+    A.xa = xa;
+    A.xb = xb;
+    A.ca = ca;
+    A.cb = cb;
+    A.x_unscaled = 0;
+    A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
+    A.precond = g->precond;
+    A.tol2 = s->tol * s->tol;
+    A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
+    A.fixed_iters = s->fixed_iters;
+    A.sumW = g->Lx * g->Ly;
+    rc = dispatch_n(g->n, [&](auto nc) { return launch_cg<double, decltype(nc)::value, float>(g, A, s->ws, st, s); });
+  } else if (s->precision != DG_FP64) {
     MixedArgs A{};
     A.omega = omega;
     A.xa = xa;
@@ -1119,7 +1137,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
   *sp = nullptr;
   if (!(D >= 0.0) || !(dt > 0.0) || !(cg_tol > 0.0) || cg_maxit < 1)
     return fail(DG_ERR_ARG, "need D >= 0, dt > 0, cg_tol > 0, cg_maxit >= 1");
-  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED64)
+  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED64 && precision != DG_FP64_PC32)
     return fail(DG_ERR_ARG, "unknown precision %d", precision);
   dg_sim* s = new (std::nothrow) dg_sim();
   if (!s) return fail(DG_ERR_NOMEM, "host allocation failed");
@@ -1150,7 +1168,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
     CUDA_TRY(cudaMalloc(&s->k3, rbytes));
     if (int rc = alloc_ws(s->ws, ndof_of(g), co_resident_cap(g), false)) return rc;
     if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision != DG_FP64)) return rc;
-    return precision != DG_FP64 ? alloc_ws_mixed(s->ws) : DG_OK;
+    return (precision == DG_MIXED || precision == DG_MIXED64) ? alloc_ws_mixed(s->ws) : DG_OK;
   };
   if (int rc = alloc_all()) {
     free_sim(s);
@@ -1872,6 +1890,7 @@ int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream) {
   for (dg_sim* t : b->sims)
     if (t == s) return fail(DG_ERR_ARG, "simulation already in the batch");
   if (s->K != 3) return fail(DG_ERR_ARG, "batched steps are AB3 (the simulation uses K = %d)", s->K);
+  if (s->precision == DG_FP64_PC32) return fail(DG_ERR_ARG, "batched simulations use DG_FP64, DG_MIXED or DG_MIXED64");
   if (s->parts != 0) return fail(DG_ERR_ARG, "batched steps use the bracket of Eq. J");
   if (s->step < 2)
     if (int rc = dg_step(s, int(2 - s->step), stream)) return rc;  // RK4 start-up steps on their own

@@ -8,6 +8,8 @@
 //   invariants_*     V, E, Omega by quadrature (Eq. quantities, Eq. def_norm)
 #pragma once
 
+#include <type_traits>
+
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -391,33 +393,47 @@ __device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& 
   __syncthreads();
 }
 
-// Cell part of the preconditioner on one tile whose interior residual is staged in X.sU:
-// z~ = Bt r~ on every cell, rc = sum sqrt(W) r~ per cell (to P.rc); returns the tile's
-// r~ . z~_block.
-template <typename T, int N>
+// Where the tile's residual is staged for the preconditioner's cell part: X.sU itself, or,
+// with a float32 preconditioner in a float64 solve, a float32 copy in the (then unused) trace
+// arrays.
+template <typename T, typename TP>
+__device__ __forceinline__ TP* pc_stage(SolveCtx<T>& X) {
+  if constexpr (std::is_same<T, TP>::value)
+    return X.sU;
+  else
+    return reinterpret_cast<TP*>(X.tXR);
+}
+
+// Cell part of the preconditioner on one tile whose interior residual is staged (X.sU, and its
+// copy in the preconditioner's precision TP): z~ = Bt r~ on every cell, rc = sum sqrt(W) r~ per
+// cell (to P.rc); returns the tile's r~ . z~_block (in T).
+template <typename T, int N, typename TP = T>
 __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const TileBox& B,
-                                      const PrecondArgs<T>& P, SolveCtx<T>& X) {
+                                      const PrecondArgs<TP>& P, SolveCtx<T>& X) {
   constexpr int NN = N * N;
+  const TP* Bs = reinterpret_cast<const TP*>(X.Bs);
+  const TP* su = pc_stage<T, TP>(X);
   T rz = T(0);
   const int nin = B.TYe * B.TXe * NN;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
-    T zj = T(0);
+    const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
+    const TP* u = su + cell;
+    TP zj = TP(0);
 #pragma unroll
-    for (int j = 0; j < NN; ++j) zj = fma(X.Bs[j * NN + k], u[j], zj);  // Bt is symmetric
+    for (int j = 0; j < NN; ++j) zj = fma(Bs[j * NN + k], u[j], zj);  // Bt is symmetric
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
     __stcg(P.z + g, zj);
-    rz = fma(u[k], zj, rz);
+    rz = fma(X.sU[cell + k], T(zj), rz);
   }
   const int ncell = B.TYe * B.TXe;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const T* u = X.sU + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
-    T v = T(0);
+    const TP* u = su + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
+    TP v = TP(0);
 #pragma unroll
-    for (int k = 0; k < NN; ++k) v = fma(C.sw[k], u[k], v);
+    for (int k = 0; k < NN; ++k) v = fma(TP(C.sw[k]), u[k], v);
     __stcg(P.rc + (size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx), v);
   }
   return rz;
@@ -442,9 +458,11 @@ __device__ __forceinline__ void st_cplx(Cplx<T>* p, Cplx<T> v) {
 // A + i B (extended by conjugate symmetry) returns row a in the real and row b in the
 // imaginary part.  Three grid-wide phases; the spectrum array holds Ny x (Nx/2 + 1) values.
 // Returns sum uc . rc (in every block).
-template <typename T>
-__device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P, SolveCtx<T>& X, T& ucrc) {
+template <typename T, typename TR = T>
+__device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P, SolveCtx<TR>& X, TR& ucrc) {
   const int Nx = G.Nx, Ny = G.Ny;
+  Cplx<T>* L0 = reinterpret_cast<Cplx<T>*>(X.line0);  // the solve's DFT line buffers, in T
+  Cplx<T>* L1 = reinterpret_cast<Cplx<T>*>(X.line1);
   const int Nh = Nx / 2, W = Nh + 1;  // kept columns
   const int npairs = (Ny + 1) / 2;
   for (int pr = X.vrank; pr < npairs; pr += X.vsize) {
@@ -453,12 +471,12 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
       const T va = __ldcg(P.rc + (size_t)ra * Nx + j);
       const T vb = hasb ? __ldcg(P.rc + (size_t)rb * Nx + j) : T(0);
-      X.line0[dft_slot(j, P.log2x)] = Cplx<T>{va, vb};
+      L0[dft_slot(j, P.log2x)] = Cplx<T>{va, vb};
     }
     __syncthreads();
-    dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, false);
+    dft_line(L0, L1, Nx, P.log2x, P.twx, false);
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
-      const Cplx<T> zk = X.line0[k], zm = X.line0[k == 0 ? 0 : Nx - k];
+      const Cplx<T> zk = L0[k], zm = L0[k == 0 ? 0 : Nx - k];
       st_cplx(&P.C[(size_t)ra * W + k], Cplx<T>{T(0.5) * (zk.re + zm.re), T(0.5) * (zk.im - zm.im)});
       if (hasb) st_cplx(&P.C[(size_t)rb * W + k], Cplx<T>{T(0.5) * (zk.im + zm.im), T(0.5) * (zm.re - zk.re)});
     }
@@ -467,21 +485,21 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
   const T scale = T(1) / (T(Nx) * T(Ny));
   for (int col = X.vrank; col < W; col += X.vsize) {
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) X.line0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * W + col]);
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) L0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * W + col]);
     __syncthreads();
-    dft_line(X.line0, X.line1, Ny, P.log2y, P.twy, false);
+    dft_line(L0, L1, Ny, P.log2y, P.twy, false);
     for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
       const T f = (col == 0 && ky == 0) ? T(0) : scale / (P.ax[col] + P.ay[ky]);
-      const Cplx<T> v = X.line0[ky];
-      X.line1[dft_slot(ky, P.log2y)] = Cplx<T>{v.re * f, v.im * f};
+      const Cplx<T> v = L0[ky];
+      L1[dft_slot(ky, P.log2y)] = Cplx<T>{v.re * f, v.im * f};
     }
     __syncthreads();
-    dft_line(X.line1, X.line0, Ny, P.log2y, P.twy, true);
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * W + col], X.line1[j]);
+    dft_line(L1, L0, Ny, P.log2y, P.twy, true);
+    for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * W + col], L1[j]);
     __syncthreads();
   }
   if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
-  T acc = T(0);
+  TR acc = TR(0);
   for (int pr = X.vrank; pr < npairs; pr += X.vsize) {
     const int ra = 2 * pr, rb = 2 * pr + 1;
     const bool hasb = rb < Ny;
@@ -495,20 +513,20 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
         A.im = -A.im;
         B.im = -B.im;
       }
-      X.line0[dft_slot(k, P.log2x)] = Cplx<T>{A.re - B.im, A.im + B.re};
+      L0[dft_slot(k, P.log2x)] = Cplx<T>{A.re - B.im, A.im + B.re};
     }
     __syncthreads();
-    dft_line(X.line0, X.line1, Nx, P.log2x, P.twx, true);
+    dft_line(L0, L1, Nx, P.log2x, P.twx, true);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) {
       const size_t ca = (size_t)ra * Nx + j;
-      const T ua = X.line0[j].re;
+      const T ua = L0[j].re;
       __stcg(P.uc + ca, ua);
-      acc = fma(ua, __ldcg(P.rc + ca), acc);
+      acc = fma(TR(ua), TR(__ldcg(P.rc + ca)), acc);
       if (hasb) {
         const size_t cb = (size_t)rb * Nx + j;
-        const T ub = X.line0[j].im;
+        const T ub = L0[j].im;
         __stcg(P.uc + cb, ub);
-        acc = fma(ub, __ldcg(P.rc + cb), acc);
+        acc = fma(TR(ub), TR(__ldcg(P.rc + cb)), acc);
       }
     }
     __syncthreads();
@@ -517,11 +535,12 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
 }
 
 // z~ = M^-1 r~ for the residual currently in r; returns r~ . z~ in rz.
-template <typename T, int N>
-__device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, const PrecondArgs<T>& P, const T* r,
+template <typename T, int N, typename TP = T>
+__device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, const PrecondArgs<TP>& P, const T* r,
                                          SolveCtx<T>& X, T& rz) {
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
+  TP* su = pc_stage<T, TP>(X);
   T rzb = T(0);
   for (int t = X.vrank; t < ntiles; t += X.vsize) {
     const TileBox B = make_box(G, t);
@@ -530,16 +549,19 @@ __device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, co
       const int c = i / NN, k = i - (i / NN) * NN;
       const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
       const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-      X.sU[((ry + 1) * B.BW + rx + 1) * (NN + 1) + k] = __ldcg(r + g);
+      const int o = ((ry + 1) * B.BW + rx + 1) * (NN + 1) + k;
+      const T v = __ldcg(r + g);
+      X.sU[o] = v;
+      if constexpr (!std::is_same<T, TP>::value) su[o] = TP(v);
     }
     __syncthreads();
-    rzb += pc_cells<T, N>(C, G, B, P, X);
+    rzb += pc_cells<T, N, TP>(C, G, B, P, X);
     __syncthreads();
   }
   T rzsum = T(0);
   if (!reduce_all(X, rzb, rzsum)) return false;
   T ucrc = T(0);
-  if (!pc_coarse(G, P, X, ucrc)) return false;
+  if (!pc_coarse<TP, T>(G, P, X, ucrc)) return false;
   rz = rzsum + ucrc;
   return true;
 }
@@ -549,9 +571,9 @@ __device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, co
 // already applied and rz = r.z.  The stopping rule is on the true residual: when the
 // recursive residual meets the tolerance, one more tile pass computes b - Ahat y; if that
 // misses the tolerance, CG restarts from it.  Returns the iteration count; raises flags.
-template <typename T, int N>
+template <typename T, int N, typename TP = T>
 __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, const CgVectors<T>& V,
-                                          const PrecondArgs<T>* P, const RhsSource<T>& Bsrc, SolveCtx<T>& X,
+                                          const PrecondArgs<TP>* P, const RhsSource<T>& Bsrc, SolveCtx<T>& X,
                                           T& rr, T rz, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
                                           int max_restarts = kMaxRestarts) {
   constexpr int NN = N * N;
@@ -592,7 +614,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       }
       ++restarts;
       if (P) {
-        if (!pc_apply<T, N>(C, G, *P, V.r, X, rz)) {
+        if (!pc_apply<T, N, TP>(C, G, *P, V.r, X, rz)) {
           flags |= kFlagTimeout;
           return it;
         }
@@ -615,7 +637,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       cg_tile_apply<T, N>(
           C, G, t, X,
           [&](size_t g, int k, bool interior) {
-            const T zv = P ? fma(C.sw[k], __ldcg(P->uc + g / NN), __ldcg(P->z + g)) : __ldcg(V.r + g);
+            const T zv = P ? fma(C.sw[k], T(__ldcg(P->uc + g / NN)), T(__ldcg(P->z + g))) : __ldcg(V.r + g);
             const T pv = first ? zv : fma(beta, __ldcg(pin + g), zv);
             if (interior) __stcg(pout + g, pv);
             return pv;
@@ -663,10 +685,12 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
           __stcg(V.y + g, yv);
           __stcg(V.r + g, rv);
           rrb = fma(rv, rv, rrb);
-          X.sU[((ry + 1) * B.BW + rx + 1) * (NN + 1) + k] = rv;
+          const int o = ((ry + 1) * B.BW + rx + 1) * (NN + 1) + k;
+          X.sU[o] = rv;
+          if constexpr (!std::is_same<T, TP>::value) pc_stage<T, TP>(X)[o] = TP(rv);
         }
         __syncthreads();
-        rzb += pc_cells<T, N>(C, G, B, *P, X);
+        rzb += pc_cells<T, N, TP>(C, G, B, *P, X);
         __syncthreads();
       }
     }
@@ -678,7 +702,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
     T rznew = rnew;
     if (P) {
       T ucrc = T(0);
-      if (!pc_coarse(G, *P, X, ucrc)) {
+      if (!pc_coarse<TP, T>(G, *P, X, ucrc)) {
         flags |= kFlagTimeout;
         return it;
       }
@@ -713,7 +737,7 @@ __device__ __forceinline__ bool project_mean(const Ops2D<T, N>& C, const Geom& G
   return grid_barrier(X.sync, X.s_flag, X.vsize);
 }
 
-template <typename T>
+template <typename T, typename TP = T>
 struct CgArgs {
   const double* omega;  // b = sqrt(W) (omega - mean_W omega) ...
   const T* rhs;         // ... or b = rhs (scaled space) when non-null
@@ -723,7 +747,7 @@ struct CgArgs {
   int x_unscaled;
   CgVectors<T> v;
   int precond;          // 0: W^-1 (plain CG on the scaled system), 1: two-level
-  PrecondArgs<T> pc;
+  PrecondArgs<TP> pc;   // (TP = float: the preconditioner applied in float32)
   double* psi_out;      // if non-null: psi = y / sqrt(W) at the end
   T* part;              // 4 * gridDim.x
   SyncState* sync;
@@ -751,15 +775,15 @@ __host__ __device__ constexpr size_t cg_smem_bytes(int TY, int TX, int Lmax, boo
 }
 
 // Lays out the solve context over dynamic shared memory starting at base (bytes).
-template <typename T, int N>
-__device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, const Geom& G, const T* Bt_global,
+template <typename T, int N, typename TB = T>
+__device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, const Geom& G, const TB* Bt_global,
                                          bool pc, int Lmax) {
   constexpr int NN = N * N;
   unsigned char* p = base;
   if (pc) {
-    T* Bs = reinterpret_cast<T*>(p);
+    TB* Bs = reinterpret_cast<TB*>(p);  // Bt in the preconditioner's precision TB (<= T)
     for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) Bs[i] = Bt_global[i];
-    X.Bs = Bs;
+    X.Bs = reinterpret_cast<const T*>(Bs);
     p += align16(sizeof(T) * NN * NN);
   } else {
     X.Bs = nullptr;
@@ -776,8 +800,9 @@ __device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, co
 }
 
 // The whole Poisson solve on the (virtual) grid of X (context laid out by init_ctx).
-template <typename T, int N>
-__device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, const CgArgs<T>& A, SolveCtx<T>& X) {
+template <typename T, int N, typename TP = T>
+__device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, const CgArgs<T, TP>& A,
+                                         SolveCtx<T>& X) {
   constexpr int NN = N * N;
   const bool pc = A.precond == 1;
   X.sync = A.sync;
@@ -836,11 +861,11 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
     for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) __stcg(A.v.y + i, T(0));
     rr = T(0);
   } else {
-    if (pc && !pc_apply<T, N>(C, G, A.pc, A.v.r, X, rz)) {
+    if (pc && !pc_apply<T, N, TP>(C, G, A.pc, A.v.r, X, rz)) {
       flags |= kFlagTimeout;
       goto finish;
     }
-    it = cg_iterate<T, N>(C, G, A.v, pc ? &A.pc : nullptr, RhsSource<T>{A.omega, A.rhs, wbar}, X, rr, rz, rhob,
+    it = cg_iterate<T, N, TP>(C, G, A.v, pc ? &A.pc : nullptr, RhsSource<T>{A.omega, A.rhs, wbar}, X, rr, rz, rhob,
                           A.tol2, A.maxit, A.fixed_iters, flags);
     if (pc && !(flags & kFlagTimeout) && !project_mean<T, N>(C, G, A.v.y, A.sumW, X)) flags |= kFlagTimeout;
   }
@@ -863,22 +888,22 @@ finish:
   }
 }
 
-template <typename T, int N>
+template <typename T, int N, typename TP = T>
 __global__ void __launch_bounds__(kThreads, 4) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
-                                                     const __grid_constant__ CgArgs<T> A) {
+                                                        const __grid_constant__ CgArgs<T, TP> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[32];
   __shared__ T bcast;
   __shared__ int s_flag;
   const Ops2D<T, N>& Cs = stage_table(C, smem_raw);
   SolveCtx<T> X;
-  init_ctx<T, N>(X, smem_raw + table_bytes<Ops2D<T, N>>(), G, A.pc.Bt, A.precond == 1, max(G.Nx, G.Ny));
+  init_ctx<T, N, TP>(X, smem_raw + table_bytes<Ops2D<T, N>>(), G, A.pc.Bt, A.precond == 1, max(G.Nx, G.Ny));
   X.red = red;
   X.bcast = &bcast;
   X.s_flag = &s_flag;
   X.vrank = blockIdx.x;
   X.vsize = gridDim.x;
-  cg_solve<T, N>(Cs, G, A, X);
+  cg_solve<T, N, TP>(Cs, G, A, X);
 }
 
 // =========================================================================================
@@ -1073,7 +1098,7 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
   Xf.vrank = blockIdx.x;
   Xf.vsize = gridDim.x;
   SolveCtx<double> Xd;
-  init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), G, nullptr, false, Lmax);
+  init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), G, (const double*)nullptr, false, Lmax);
   Xd.red = redd;
   Xd.bcast = &bcd;
   Xd.s_flag = &s_flag;
@@ -1228,7 +1253,7 @@ __device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, 
     Xf.vrank = vrank;
     Xf.vsize = grp.nblocks;
     SolveCtx<double> Xd;
-    init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), S.Gc, nullptr, false, Lmax);
+    init_ctx<double, N>(Xd, smem + (pc ? align16(sizeof(float) * NN * NN) : 0), S.Gc, (const double*)nullptr, false, Lmax);
     Xd.red = redd;
     Xd.bcast = bcd;
     Xd.s_flag = s_flag;

@@ -11,7 +11,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT, DG_ERR_IO = range(8)
-DG_FP64, DG_MIXED, DG_MIXED64 = 0, 1, 2
+DG_FP64, DG_MIXED, DG_MIXED64, DG_FP64_PC32 = 0, 1, 2, 3
 DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
 DG_BRACKET_ARAKAWA, DG_BRACKET_NAIVE = 0, 1
 

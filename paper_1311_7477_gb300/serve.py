@@ -22,7 +22,8 @@ from . import dg, workloads
 
 # device bytes per dof of one simulation (state rings, RK stages, solver and preconditioner
 # vectors, grid workspace), float64 / mixed
-BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 21 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10}
+BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 21 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10,
+                 dg.DG_FP64_PC32: 8 * 23 + 4 * 2}
 
 
 def footprint(N, n, precision):
