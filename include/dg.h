@@ -214,11 +214,12 @@ typedef struct {
 
 /*
  * dg_sim_create -- a simulation on grid g (which must outlive it) with viscosity D >= 0,
- * time step dt > 0, precision DG_FP64 or DG_MIXED, CG tolerance cg_tol > 0 and iteration
- * cap cg_maxit, from the device field omega0.  Solves for psi0 at creation.  The scheme is
- * the explicit 3-step Adams-Bashforth method (Sec. 6) for
+ * time step dt > 0, precision DG_FP64, DG_MIXED, DG_MIXED64 or DG_FP64_PC32, CG tolerance
+ * cg_tol > 0 and iteration cap cg_maxit, from the device field omega0.  Solves for psi0 at
+ * creation.  The scheme is the explicit K-step Adams-Bashforth method (Sec. 6; K = 3 unless
+ * dg_sim_set_multistep changes it) for
  *     R(omega) = -J(psi, omega) + D Delta_h omega,
- * the first two steps being classical RK4 steps of the same dt; each Poisson solve starts
+ * the first K-1 steps being classical RK4 steps of the same dt; each Poisson solve starts
  * from the extrapolation 2 psi^k - psi^{k-1} of the last two solutions (Sec. 6).
  * Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_CUDA.
  */
