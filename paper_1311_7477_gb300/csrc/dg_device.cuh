@@ -275,23 +275,48 @@ __device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
 // In-place DFT of one line of length L held in shared memory s[0..L), computed by the
 // whole block.  tw[m] = exp(-2 pi i m / L), m < L (host-computed).  inverse: conjugate
 // twiddles (no 1/L factor).  Power-of-two L: iterative radix-2 decimation in time on
-// bit-reversed input (the caller loads s[bitrev(j)] = x[j]); otherwise a direct O(L^2) sum
-// into tmp[0..L) copied back.
+// bit-reversed input (the caller loads s[bitrev(j)] = x[j]), two stages per pass;
+// otherwise a direct O(L^2) sum into tmp[0..L) copied back.
 template <typename T>
 __device__ __forceinline__ void dft_line(Cplx<T>* s, Cplx<T>* tmp, int L, int log2L, const Cplx<T>* tw,
                                          bool inverse) {
   if (log2L >= 0) {
-    for (int half = 1; half < L; half <<= 1) {
-      const int stride = L / (2 * half);
+    int half = 1;
+    if (log2L & 1) {  // an odd number of stages: one radix-2 stage first
       for (int t = threadIdx.x; t < L / 2; t += blockDim.x) {
-        const int grp = t / half, pos = t - (t / half) * half;
-        const int i1 = grp * 2 * half + pos, i2 = i1 + half;
-        Cplx<T> w = tw[pos * stride];
+        Cplx<T> w = tw[0];
         if (inverse) w.im = -w.im;
-        const Cplx<T> u = s[i1];
-        const Cplx<T> v = cmul(w, s[i2]);
-        s[i1] = Cplx<T>{u.re + v.re, u.im + v.im};
-        s[i2] = Cplx<T>{u.re - v.re, u.im - v.im};
+        const Cplx<T> u = s[2 * t];
+        const Cplx<T> v = cmul(w, s[2 * t + 1]);
+        s[2 * t] = Cplx<T>{u.re + v.re, u.im + v.im};
+        s[2 * t + 1] = Cplx<T>{u.re - v.re, u.im - v.im};
+      }
+      __syncthreads();
+      half = 2;
+    }
+    // two radix-2 stages (half, 2 half) per pass over groups of four: half the block
+    // synchronisations of one stage per pass
+    for (; half < L; half <<= 2) {
+      const int s2 = L / (2 * half), s4 = L / (4 * half);
+      for (int t = threadIdx.x; t < L / 4; t += blockDim.x) {
+        const int grp = t / half, pos = t - grp * half;
+        const int i0 = grp * 4 * half + pos;
+        Cplx<T> w2 = tw[pos * s2], w4 = tw[pos * s4];
+        if (inverse) {
+          w2.im = -w2.im;
+          w4.im = -w4.im;
+        }
+        const Cplx<T> a = s[i0], b = cmul(w2, s[i0 + half]);
+        const Cplx<T> c = s[i0 + 2 * half], d = cmul(w2, s[i0 + 3 * half]);
+        const Cplx<T> A1{a.re + b.re, a.im + b.im}, B1{a.re - b.re, a.im - b.im};
+        const Cplx<T> C1 = cmul(w4, Cplx<T>{c.re + d.re, c.im + d.im});
+        Cplx<T> D1 = cmul(w4, Cplx<T>{c.re - d.re, c.im - d.im});
+        // the second stage's twiddle for the odd half is w4 times exp(-+ i pi / 2)
+        D1 = inverse ? Cplx<T>{-D1.im, D1.re} : Cplx<T>{D1.im, -D1.re};
+        s[i0] = Cplx<T>{A1.re + C1.re, A1.im + C1.im};
+        s[i0 + 2 * half] = Cplx<T>{A1.re - C1.re, A1.im - C1.im};
+        s[i0 + half] = Cplx<T>{B1.re + D1.re, B1.im + D1.im};
+        s[i0 + 3 * half] = Cplx<T>{B1.re - D1.re, B1.im - D1.im};
       }
       __syncthreads();
     }
