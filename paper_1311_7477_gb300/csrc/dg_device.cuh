@@ -260,6 +260,13 @@ __device__ __forceinline__ bool grid_barrier(SyncState* s, int* s_flag, unsigned
   return *s_flag == 0;
 }
 
+// All threads of all blocks of this thread-block cluster meet here: the hardware cluster
+// barrier, with release / acquire ordering of memory (global included) at cluster scope.
+// The blocks of a cluster are co-scheduled by construction, so the wait needs no cap.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ---- lines of a 2D DFT in shared memory ---------------------------------------------------
 
 template <typename T>

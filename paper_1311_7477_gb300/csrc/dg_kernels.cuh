@@ -340,7 +340,19 @@ struct SolveCtx {
   T* part;                        // 4 * vsize: two alternating halves
   int phase;
   int vrank, vsize;               // this block's rank and the block count of the (virtual) grid
+  int cluster;                    // the whole grid is one thread-block cluster
 };
+
+// The barrier between the phases of a solve: the hardware cluster barrier when the solve's
+// blocks form one cluster (small grids), else the capped grid barrier.
+template <typename T>
+__device__ __forceinline__ bool solve_barrier(SolveCtx<T>& X) {
+  if (X.cluster) {
+    cluster_barrier();
+    return true;
+  }
+  return grid_barrier(X.sync, X.s_flag, X.vsize);
+}
 
 // Block partials of one or two sums -> grid barrier -> the sums in every block (fixed order).
 template <typename T>
@@ -349,7 +361,7 @@ __device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
   ++X.phase;
   v0 = block_sum(v0, X.red);
   if (threadIdx.x == 0) __stcg(ph + X.vrank, v0);
-  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  if (!solve_barrier(X)) return false;
   out0 = sum_partials_block(ph, X.vsize, 1, X.red, X.bcast);
   return true;
 }
@@ -362,7 +374,7 @@ __device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0,
   if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank, v0);
   v1 = block_sum(v1, X.red);
   if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank + 1, v1);
-  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  if (!solve_barrier(X)) return false;
   out0 = sum_partials_block(ph, X.vsize, 2, X.red, X.bcast);
   out1 = sum_partials_block(ph + 1, X.vsize, 2, X.red, X.bcast);
   return true;
@@ -482,7 +494,7 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
     }
     __syncthreads();
   }
-  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  if (!solve_barrier(X)) return false;
   const T scale = T(1) / (T(Nx) * T(Ny));
   for (int col = X.vrank; col < W; col += X.vsize) {
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) L0[dft_slot(j, P.log2y)] = ld_cplx(&P.C[(size_t)j * W + col]);
@@ -498,7 +510,7 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) st_cplx(&P.C[(size_t)j * W + col], L1[j]);
     __syncthreads();
   }
-  if (!grid_barrier(X.sync, X.s_flag, X.vsize)) return false;
+  if (!solve_barrier(X)) return false;
   TR acc = TR(0);
   for (int pr = X.vrank; pr < npairs; pr += X.vsize) {
     const int ra = 2 * pr, rb = 2 * pr + 1;
@@ -734,7 +746,7 @@ __device__ __forceinline__ bool project_mean(const Ops2D<T, N>& C, const Geom& G
   m = m / T(sumW);
   for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
     __stcg(y + i, fma(-m, C.sw[i % NN], __ldcg(y + i)));
-  return grid_barrier(X.sync, X.s_flag, X.vsize);
+  return solve_barrier(X);
 }
 
 template <typename T, typename TP = T>
@@ -755,6 +767,7 @@ struct CgArgs {
   double tol2;
   int maxit, fixed_iters;
   double sumW;
+  int cluster;          // launched as one thread-block cluster (cluster barriers)
 };
 
 // Dynamic shared memory of the persistent solves: [Bt (with the preconditioner)] then one
@@ -796,6 +809,7 @@ __device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, co
   X.tYL = X.tYR + boxc * N;
   X.line0 = reinterpret_cast<Cplx<T>*>(p);
   X.line1 = X.line0 + Lmax;
+  X.cluster = 0;
   __syncthreads();
 }
 
@@ -903,6 +917,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_kernel(const __grid_constant__
   X.s_flag = &s_flag;
   X.vrank = blockIdx.x;
   X.vsize = gridDim.x;
+  X.cluster = A.cluster;
   cg_solve<T, N, TP>(Cs, G, A, X);
 }
 
@@ -933,6 +948,7 @@ struct MixedArgs {
   double tol2, tol_in2;
   int max_sweeps, maxit_in;
   double sumW;
+  int cluster;         // launched as one thread-block cluster (cluster barriers)
 };
 
 template <int N>
@@ -988,7 +1004,6 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   Xd.sync = A.sync;
   Xd.part = A.partd;
   Xd.phase = 0;
-  int* s_flag_ptr = Xd.s_flag;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)Xd.vsize * blockDim.x;
   int flags = 0, sweeps = 0;
@@ -1047,7 +1062,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
     // y += e
     for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       __stcg(A.y + i, __ldcg(A.y + i) + double(__ldcg(A.v.y + i)));
-    if (!grid_barrier(A.sync, s_flag_ptr, Xd.vsize)) {
+    if (!solve_barrier(Xd)) {
       flags |= kFlagTimeout;
       goto finish;
     }
@@ -1104,6 +1119,7 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
   Xd.s_flag = &s_flag;
   Xd.vrank = blockIdx.x;
   Xd.vsize = gridDim.x;
+  Xf.cluster = Xd.cluster = A.cluster;
   mixed_solve<N>(Cds, Cfs, G, A, Xf, Xd);
 }
 
