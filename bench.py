@@ -293,6 +293,25 @@ def _config(name, wl, precision):
 
 
 # ----------------------------------------------------------------------------------------
+# multi-GPU bookkeeping: one independent simulation (replica) per rank, no collective in the
+# data path; the elapsed time is the maximum over ranks and the rate counts every rank's dof
+# ----------------------------------------------------------------------------------------
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank float over all ranks (x itself with one process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(dof_per_rank, steps, world, seconds):
+    """Mdof.steps/s of the whole job: every rank advances its own dof_per_rank replica."""
+    return dof_per_rank * steps * world / seconds / 1e6
+
+
+# ----------------------------------------------------------------------------------------
 # native arm
 # ----------------------------------------------------------------------------------------
 def main():
@@ -378,10 +397,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     info1 = sim.status()
     cnt = sim.counters()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     iters = (info1.cg_iters_total - info0.cg_iters_total) / max(args.steps, 1)
 
     # --- end to end through the host-buffer entry points: resume a checkpoint from pinned
@@ -402,11 +418,7 @@ def main():
         sim.invariants()
     sim.download(hout[0], hout[1])
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
 
     # --- mixed precision: error of one step against the float64 path from the identical state
     err_vs_fp64 = None
@@ -476,7 +488,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    value = dof * args.steps * world / (ms / 1e3) / 1e6
+    value = whole_job_rate(dof, args.steps, world, ms / 1e3)
     peaks, peak_src = measured_peaks()
     # roofline of the dominant kernel (the persistent CG solve), from its live event timing
     cg_ms_per_launch = cnt.cg_ms / max(cnt.cg_launches, 1)
