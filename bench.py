@@ -329,6 +329,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-steps-scale", type=float, default=0.02)
     ap.add_argument("--serve-max-cells", type=int, default=1024)
+    ap.add_argument("--serve-groups", type=int, default=0, help="block groups of the batch (0: automatic)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -754,13 +755,14 @@ def run_serve(args):
     for r, f in zip(trace, fields_):
         r["omega0"] = f
     t_gen = time.perf_counter() - t_gen
-    srv = serve.Server(max_active=64, hbm_budget=200e9, precision=prec, precond=args.precond)
+    srv = serve.Server(max_active=64, hbm_budget=200e9, precision=prec, precond=args.precond,
+                       groups=args.serve_groups)
     rep = srv.run(trace)
     line = {"metric": "Mdof·steps/s", "value": rep["mdof_steps_per_s"], "unit": "Mdof·steps/s", "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "serve", "requests": len(trace), "rate_per_s": 20, "cells": list(Ns),
-                       "n": [3, 4, 5], "steps_scale": args.serve_steps_scale,
+                       "n": [3, 4, 5], "steps_scale": args.serve_steps_scale, "groups": args.serve_groups,
                        "precision": {0: "fp64", 1: "mixed", 2: "mixed64"}[prec], "cg_preconditioner": args.precond},
             "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
             "served": rep, "field_generation_s_before_clock": t_gen}

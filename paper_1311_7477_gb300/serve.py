@@ -51,8 +51,10 @@ class Request:
 
 class Server:
     def __init__(self, max_active=64, hbm_budget=200e9, precision=dg.DG_MIXED, precond="twolevel", cg_tol=1e-10,
-                 chunk=8, dt_cap=2e-4, keep_results=False):
+                 chunk=8, dt_cap=2e-4, keep_results=False, groups=0):
         self.batch = dg.Batch(max_active)
+        if groups:
+            self.batch.set_groups(groups)
         self.max_active = max_active
         self.budget = float(hbm_budget)
         self.precision = precision
