@@ -103,6 +103,18 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
   const int wx = B.TXe + 2, hx = y1 - y0;   // x-line cells: rows y0..y1-1, cols -1..TXe
   const int wy = x1 - x0, hy = B.TYe + 2;   // y-line cells: rows -1..TYe, cols x0..x1-1
   const int nx = hx * wx * N, ny = hy * wy * N;
+  // the trace coefficients: in registers for float32 (for float64 the registers are scarcer
+  // than the shared-memory issue slots of this FMA-bound path)
+  T xr[N], xs[N], yr[N], ys[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if constexpr (sizeof(T) == 4) {
+      xr[j] = ox.r[j];
+      xs[j] = ox.s[j];
+      yr[j] = oy.r[j];
+      ys[j] = oy.s[j];
+    }
+  }
   for (int i = threadIdx.x; i < nx + ny; i += blockDim.x) {
     if (i < nx) {
       const int c = i / N, line = i - (i / N) * N;
@@ -112,8 +124,13 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
       T tr = T(0), tl = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        tr = fma(ox.r[j], u[j], tr);
-        tl = fma(ox.s[j], u[j], tl);
+        if constexpr (sizeof(T) == 4) {
+          tr = fma(xr[j], u[j], tr);
+          tl = fma(xs[j], u[j], tl);
+        } else {
+          tr = fma(ox.r[j], u[j], tr);
+          tl = fma(ox.s[j], u[j], tl);
+        }
       }
       tXR[lc * N + line] = tr;
       tXL[lc * N + line] = tl;
@@ -126,8 +143,13 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
       T tr = T(0), tl = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        tr = fma(oy.r[j], u[j * N], tr);
-        tl = fma(oy.s[j], u[j * N], tl);
+        if constexpr (sizeof(T) == 4) {
+          tr = fma(yr[j], u[j * N], tr);
+          tl = fma(ys[j], u[j * N], tl);
+        } else {
+          tr = fma(oy.r[j], u[j * N], tr);
+          tl = fma(oy.s[j], u[j * N], tl);
+        }
       }
       tYR[lc * N + line] = tr;
       tYL[lc * N + line] = tl;

@@ -392,15 +392,46 @@ __device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& 
   line_traces<T, N>(B, X.sU, X.sU, C.kx, C.ky, X.tXR, X.tXL, X.tYR, X.tYL, false);
   __syncthreads();
   const int nin = B.TYe * B.TXe * NN;
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-    const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const int lc = (ry + 1) * B.BW + rx + 1;
-    const int a = k / N, b = k - (k / N) * N;
-    const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
-                op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
-    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-    out(g, k, X.sU[lc * (NN + 1) + k], q);
+  if constexpr (sizeof(T) == 4 && kThreads % NN == 0) {
+    // float32: every node a thread visits is node k = threadIdx.x mod n^2 of its cell, so the
+    // operator rows of that node are held in registers across the thread's cells (same
+    // arithmetic and order as op_x_at / op_y_at)
+    const int k = threadIdx.x % NN, a = k / N, b = k % N;
+    T mx[N], my[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      mx[j] = C.kx.M[b][j];
+      my[j] = C.ky.M[a][j];
+    }
+    const T xa = C.kx.a[b], xd = C.kx.d[b], ya = C.ky.a[a], yd = C.ky.d[a];
+    for (int i = threadIdx.x; i < nin; i += kThreads) {
+      const int c = i / NN;
+      const int ry = c / B.TXe, rx = c - ry * B.TXe;
+      const int lc = (ry + 1) * B.BW + rx + 1;
+      const T* ux = X.sU + lc * (NN + 1) + a * N;
+      const T* uy = X.sU + lc * (NN + 1) + b;
+      T qx = xa * X.tXR[(lc + 1) * N + a];
+      qx = fma(xd, X.tXL[(lc - 1) * N + a], qx);
+#pragma unroll
+      for (int j = 0; j < N; ++j) qx = fma(mx[j], ux[j], qx);
+      T qy = ya * X.tYR[(lc + B.BW) * N + b];
+      qy = fma(yd, X.tYL[(lc - B.BW) * N + b], qy);
+#pragma unroll
+      for (int j = 0; j < N; ++j) qy = fma(my[j], uy[j * N], qy);
+      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+      out(g, k, X.sU[lc * (NN + 1) + k], qx + qy);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+      const int c = i / NN, k = i - (i / NN) * NN;
+      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+      const int lc = (ry + 1) * B.BW + rx + 1;
+      const int a = k / N, b = k - (k / N) * N;
+      const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
+                  op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
+      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+      out(g, k, X.sU[lc * (NN + 1) + k], q);
+    }
   }
   __syncthreads();
 }
@@ -427,17 +458,38 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
   const TP* su = pc_stage<T, TP>(X);
   T rz = T(0);
   const int nin = B.TYe * B.TXe * NN;
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-    const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-    const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
-    const TP* u = su + cell;
-    TP zj = TP(0);
+  if constexpr (sizeof(TP) == 4 && kThreads % NN == 0) {
+    // float32: a thread's nodes all have k = threadIdx.x mod n^2, so its column of Bt stays in
+    // registers (same arithmetic and order as below)
+    const int k = threadIdx.x % NN;
+    TP bk[NN];
 #pragma unroll
-    for (int j = 0; j < NN; ++j) zj = fma(Bs[j * NN + k], u[j], zj);  // Bt is symmetric
-    const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-    __stcg(P.z + g, zj);
-    rz = fma(X.sU[cell + k], T(zj), rz);
+    for (int j = 0; j < NN; ++j) bk[j] = Bs[j * NN + k];
+    for (int i = threadIdx.x; i < nin; i += kThreads) {
+      const int c = i / NN;
+      const int ry = c / B.TXe, rx = c - ry * B.TXe;
+      const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
+      const TP* u = su + cell;
+      TP zj = TP(0);
+#pragma unroll
+      for (int j = 0; j < NN; ++j) zj = fma(bk[j], u[j], zj);
+      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+      __stcg(P.z + g, zj);
+      rz = fma(X.sU[cell + k], T(zj), rz);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+      const int c = i / NN, k = i - (i / NN) * NN;
+      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+      const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
+      const TP* u = su + cell;
+      TP zj = TP(0);
+#pragma unroll
+      for (int j = 0; j < NN; ++j) zj = fma(Bs[j * NN + k], u[j], zj);  // Bt is symmetric
+      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+      __stcg(P.z + g, zj);
+      rz = fma(X.sU[cell + k], T(zj), rz);
+    }
   }
   const int ncell = B.TYe * B.TXe;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
