@@ -955,7 +955,7 @@ finish:
 }
 
 template <typename T, int N, typename TP = T>
-__global__ void __launch_bounds__(kThreads, 3) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+__global__ void __launch_bounds__(kThreads, N == 5 ? 4 : 3) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
                                                         const __grid_constant__ CgArgs<T, TP> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[32];
