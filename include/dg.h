@@ -355,6 +355,13 @@ int dg_batch_destroy(dg_batch* b);
 int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream);
 int dg_batch_retire(dg_batch* b, dg_sim* s);
 int dg_batch_size(const dg_batch* b);
+/*
+ * dg_batch_set_limit -- s takes no batched step beyond step index last_step (0: no limit):
+ * within a dg_batch_step of nsteps, a member that reaches its limit sits the remaining steps
+ * out, so members with different step budgets share launches of a fixed length.
+ * Errors: DG_ERR_ARG.
+ */
+int dg_batch_set_limit(dg_batch* b, dg_sim* s, long long last_step);
 int dg_batch_set_groups(dg_batch* b, int ngroups);
 int dg_batch_step(dg_batch* b, int nsteps, void* stream);
 int dg_batch_status(dg_batch* b, int* uses_graph, int* ngroups, long long* launches, void* stream);

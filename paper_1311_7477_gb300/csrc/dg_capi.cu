@@ -216,6 +216,7 @@ struct dg_grid {
 
 struct dg_sim {
   dg_grid* g;
+  long long batch_limit = 0;  // batched steps stop at this step index (0: no limit)
   double D, dt, tol;
   int precision, maxit, fixed_iters;
   long long step;
@@ -1764,6 +1765,7 @@ BatchSim make_batch_sim(dg_sim* s) {
   b.r3 = s->r3;
   b.rfree = s->rfree;
   b.step = s->step;
+  b.limit = s->batch_limit;
   b.D = s->D;
   b.dt = s->dt;
   b.tol2 = s->tol * s->tol;
@@ -1907,6 +1909,7 @@ int batch_enqueue(dg_batch* b, int nsteps, cudaStream_t st) {
 void batch_advance_host(dg_batch* b, int nsteps) {
   for (dg_sim* s : b->sims)
     for (int k = 0; k < nsteps; ++k) {
+      if (s->batch_limit > 0 && s->step >= s->batch_limit) break;
       s->oc ^= 1;
       const int p0 = s->p0, p1 = s->p1, p2 = s->p2;
       s->p0 = p2;
@@ -1991,6 +1994,14 @@ int dg_batch_retire(dg_batch* b, dg_sim* s) {
 }
 
 int dg_batch_size(const dg_batch* b) { return b ? (int)b->sims.size() : 0; }
+
+int dg_batch_set_limit(dg_batch* b, dg_sim* s, long long last_step) {
+  if (!b || !s || last_step < 0) return fail(DG_ERR_ARG, "bad arguments");
+  s->batch_limit = last_step;
+  for (dg_sim* t : b->sims)
+    if (t == s) b->dirty = true;  // the limit travels with the plan's descriptors
+  return DG_OK;
+}
 
 int dg_batch_set_groups(dg_batch* b, int ngroups) {
   if (!b || ngroups < 0) return fail(DG_ERR_ARG, "bad arguments");

@@ -1192,6 +1192,7 @@ struct BatchSim {
   void* R[4];                      // float64, or float32 with a float32 RHS
   int oc, p0, p1, p2, r1, r2, r3, rfree;  // ring indices, advanced by the kernel
   long long step;
+  long long limit;                 // no batched step once step == limit (0: no limit)
   double D, dt, tol2, tol_in2;
   int maxit, max_sweeps, fixed_iters;
   double sumW;
@@ -1252,6 +1253,9 @@ __device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, 
                                            double* redd, double* bcd, float* redf, float* bcf, int* s_flag) {
   constexpr int NN = N * N;
   const BatchSim& S = *Sp;
+  // a simulation that has reached its step limit sits the step out (every block of the
+  // group reads the same step index: it was written before the group's last barrier)
+  if (S.limit > 0 && __ldcg(&Sp->step) >= S.limit) return true;
   const int oc = __ldcg(&Sp->oc), p0 = __ldcg(&Sp->p0), p1 = __ldcg(&Sp->p1), p2 = __ldcg(&Sp->p2);
   const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), r3 = __ldcg(&Sp->r3), rfree = __ldcg(&Sp->rfree);
   // this simulation's operator tables, staged in shared memory (the previous step's last

@@ -74,6 +74,7 @@ def _load():
         "dg_sim_get_history": (I, [P, I, P, P]),
         "dg_sim_set_history": (I, [P, I, P, P]),
         "dg_sim_set_multistep": (I, [P, I]),
+        "dg_batch_set_limit": (I, [P, P, LL]),
         "dg_sim_set_bracket": (I, [P, I]),
         "dg_sim_save": (I, [P, ctypes.c_char_p, P]),
         "dg_sim_load": (I, [PP, P, ctypes.c_char_p, P]),
@@ -373,6 +374,10 @@ class Batch:
 
     def set_groups(self, ngroups):
         _check(_lib.dg_batch_set_groups(self.h, int(ngroups)))
+
+    def set_limit(self, sim, last_step):
+        """sim takes no batched step beyond step index last_step (0: no limit)."""
+        _check(_lib.dg_batch_set_limit(self.h, sim.h, int(last_step)))
 
     def step(self, nsteps=1, stream=None):
         _check(_lib.dg_batch_step(self.h, int(nsteps), _stream(stream)))

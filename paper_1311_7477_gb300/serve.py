@@ -117,6 +117,7 @@ class Server:
             sim.step(req.steps)
             req.remaining = 0
         else:
+            self.batch.set_limit(sim, req.steps)   # batched steps stop at the request's count
             self.batch.admit(sim)          # the two RK4 start-up steps run here
             req.remaining = req.steps - 2
         t3 = clock()
@@ -210,16 +211,19 @@ class Server:
                     ev.record()
                     inflight.append((ev, done_now))
                 # the next batched step, for every member with steps left
+                # (launches of a fixed length: a member whose budget ends inside a launch
+                # stops there by its step limit)
                 runnable = [r for r in self.active if r.remaining > 0]
                 if runnable:
-                    k = min(self.chunk, min(r.remaining for r in runnable))
+                    k = self.chunk
                     ts = clock()
                     self.batch.step(k)
                     self.t["step"] += clock() - ts
                     launches += 1
                     for r in runnable:
-                        r.remaining -= k
-                        self.dof_steps += r.dof * k
+                        taken = min(k, r.remaining)
+                        r.remaining -= taken
+                        self.dof_steps += r.dof * taken
                 if not runnable and not admitted:
                     if inflight:
                         inflight[0][0].synchronize()

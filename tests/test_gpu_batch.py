@@ -99,3 +99,28 @@ def test_batch_graph_retire_readmit(dg):
         wb, _ = _state(gb, sb)
         assert np.linalg.norm(wa - wb) / np.linalg.norm(wa) < 1e-8
         assert sb.status().step == k
+
+
+def test_batch_step_limits(dg):
+    """Members with different step budgets share launches of a fixed length: each stops at
+    its limit (dg_batch_set_limit) and matches the same number of steps taken alone."""
+    specs = SPECS[:3]
+    limits = [4, 7, 0]                  # step indices; 0: no limit
+    members = [_make(dg, *spec, fixed=False) for spec in specs]
+    ref = [_make(dg, *spec, fixed=False) for spec in specs]
+    b = dg.Batch(8)
+    for (g, s), lim in zip(members, limits):
+        b.set_limit(s, lim)
+        b.admit(s)
+    b.step(3)
+    b.step(3)                           # 2 start-up + 6 batched, unless limited
+    expect = [4, 7, 8]
+    for (g, s), k in zip(ref, expect):
+        s.step(k)
+    for (ga, sa), (gb, sb), k in zip(ref, members, expect):
+        assert sb.status().step == k
+        wa, _ = _state(ga, sa)
+        wb, _ = _state(gb, sb)
+        assert np.linalg.norm(wa - wb) / np.linalg.norm(wa) < 1e-8
+    with pytest.raises(RuntimeError):
+        b.set_limit(members[0][1], -1)
