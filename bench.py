@@ -42,8 +42,8 @@ WORKLOADS = {
 TABLE1_MS = {1: (0.05, 0.08), 2: (0.26, 0.52), 3: (0.71, 3.85), 4: (1.47, 9.08)}
 DEFAULT_WORKLOAD = "shear512_n4"
 L2_BYTES = 129 * 1024 * 1024
-# FP64 FMA peak of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (recipe's unit counts
-# and maximum SM clock; the microbenchmark of the design doc measured 1.20 TFLOP/s at ~2.0 GHz).
+# FP64 FMA peak of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (unit counts and
+# maximum SM clock; a dependent-chain DFMA microbenchmark measured 1.20 TFLOP/s at ~2.0 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 

@@ -18,7 +18,7 @@ states only that a conjugate gradient method solves it; the details below are a 
 With x0 of W-mean zero all iterates stay W-mean zero, since every update direction
 z = W^{-1} r satisfies sum W z = sum r = 0.
 
-A second preconditioner (a choice of this build; Sec. 6 names none) is the additive
+A second preconditioner (a design choice; Sec. 6 names none) is the additive
 two-level one of TwoLevel below: exact solves on every cell plus an exact solve of the
 Galerkin coarse problem on cell averages.  It leaves the solution unchanged and makes the
 iteration count independent of the mesh size.

@@ -1,4 +1,4 @@
-"""Pins for the oracle's two-level preconditioner (a choice of this build: Sec. 6 names
+"""Pins for the oracle's two-level preconditioner (a design choice: Sec. 6 names
 none).  It must not change what CG converges to, must be symmetric positive definite, its
 coarse solve must invert the Galerkin coarse operator exactly, and the iteration count must
 grow far more slowly with the mesh than with W^{-1} (the point of the coarse level; with
