@@ -148,19 +148,22 @@ def _gpu_index_for_smi(local_rank):
 # ----------------------------------------------------------------------------------------
 # oracle sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------------------
-SAMPLE_CELLS = 128
+SAMPLE_CELLS = 128          # reference arm: one full oracle step per timed step
+BASELINE_CELLS = 256        # cpu_baseline: full oracle steps, repeated to about 10 s
+BASELINE_SECONDS = 10.0
 
 
-def oracle_sample(wl, cg_sample_iters=4, precond="twolevel"):
-    """Times the FP64 oracle on a SAMPLE_CELLS^2 periodic grid of the same n, field and
-    parameters: one right-hand side (bracket + viscous term + AB3 update), the Poisson setup
-    and cg_sample_iters CG iterations with the given preconditioner.  Returns seconds per dof
-    for each part (the oracle's cost is linear in the dof count, up to the log of its FFT)."""
+def oracle_sample(wl, cg_sample_iters=4, precond="twolevel", cells=SAMPLE_CELLS, min_seconds=0.0):
+    """Times the FP64 oracle on a cells^2 periodic grid of the same n, field and parameters:
+    one right-hand side (bracket + viscous term + AB3 update), the Poisson setup and
+    cg_sample_iters CG iterations with the given preconditioner -- repeated until min_seconds
+    of CPU time have been spent (at least once).  Returns seconds per dof for each part (the
+    oracle's cost is linear in the dof count, up to the log of its FFT)."""
     import numpy as np
     from oracle.operators import Operators
     from oracle.solver import TwoLevel, pcg, poisson_rhs
     from oracle.tables import Grid
-    g = Grid(SAMPLE_CELLS, SAMPLE_CELLS, wl["n"])
+    g = Grid(cells, cells, wl["n"])
     ops = Operators(g)
     M = TwoLevel(ops) if precond == "twolevel" else None
     X, Y = g.mesh()
@@ -168,19 +171,26 @@ def oracle_sample(wl, cg_sample_iters=4, precond="twolevel"):
     psi = 0.01 * np.sin(X) * np.cos(Y)
     R1 = np.zeros_like(w)
     dof = w.size
-    t0 = time.perf_counter()
-    R = -ops.bracket(psi, w)
-    if wl["D"] != 0.0:
-        R = R + wl["D"] * ops.laplacian(w)
-    w1 = w + wl["dt"] * (23.0 * R - 16.0 * R1 + 5.0 * R1) / 12.0
-    t1 = time.perf_counter()
-    b = poisson_rhs(ops, w1)
-    t2 = time.perf_counter()
-    pcg(ops, b, psi, 1e-30, cg_sample_iters, fixed_iters=cg_sample_iters, precond=M)
-    t3 = time.perf_counter()
+    t_rhs = t_setup = t_cg = 0.0
+    reps = 0
+    while reps == 0 or t_rhs + t_setup + t_cg < min_seconds:
+        t0 = time.perf_counter()
+        R = -ops.bracket(psi, w)
+        if wl["D"] != 0.0:
+            R = R + wl["D"] * ops.laplacian(w)
+        w1 = w + wl["dt"] * (23.0 * R - 16.0 * R1 + 5.0 * R1) / 12.0
+        t1 = time.perf_counter()
+        b = poisson_rhs(ops, w1)
+        t2 = time.perf_counter()
+        pcg(ops, b, psi, 1e-30, cg_sample_iters, fixed_iters=cg_sample_iters, precond=M)
+        t3 = time.perf_counter()
+        t_rhs, t_setup, t_cg = t_rhs + (t1 - t0), t_setup + (t2 - t1), t_cg + (t3 - t2)
+        reps += 1
     # pcg includes one setup apply (r0 = b - A x0) besides the iterations
-    return {"rhs_s_per_dof": (t1 - t0) / dof, "setup_s_per_dof": (t2 - t1) / dof,
-            "cg_s_per_dof_iter": (t3 - t2) / dof / (cg_sample_iters + 1), "sample_dof": dof}
+    return {"rhs_s_per_dof": t_rhs / reps / dof, "setup_s_per_dof": t_setup / reps / dof,
+            "cg_s_per_dof_iter": t_cg / reps / dof / (cg_sample_iters + 1), "sample_dof": dof,
+            "cells": cells, "reps": reps, "cg_iters": cg_sample_iters,
+            "cpu_s": t_rhs + t_setup + t_cg}
 
 
 def oracle_iters_per_step(name, precond="twolevel"):
@@ -193,29 +203,30 @@ def oracle_iters_per_step(name, precond="twolevel"):
 
 
 def cpu_baseline(name, wl, native_iters, precond="twolevel", threads=1):
-    """Runs the oracle sample in a child process with the given number of BLAS/OpenMP
-    threads; returns the cpu_baseline object of the JSON line."""
+    """Runs the oracle sample (full steps on a BASELINE_CELLS^2 grid, about BASELINE_SECONDS
+    of CPU time) in a child process with the given number of BLAS/OpenMP threads; returns the
+    cpu_baseline object of the JSON line."""
+    k, ksrc = oracle_iters_per_step(name, precond)
+    if k is None:
+        k, ksrc = native_iters, "CG iterations per step measured on the GPU in this run"
+    kint = max(1, int(round(k)))
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ("import json,sys; sys.path.insert(0,%r); import bench; "
-            "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r], 4, %r)))" % (ROOT, name, precond))
-    t0 = time.time()
+            "print(json.dumps(bench.oracle_sample(bench.WORKLOADS[%r], %d, %r, %d, %r)))"
+            % (ROOT, name, kint, precond, BASELINE_CELLS, BASELINE_SECONDS))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         return {"value": None, "unit": "Mdof·steps/s", "cores": threads, "kind": "oracle",
                 "sample": "failed: " + out.stderr.strip()[-200:]}
     s = json.loads(out.stdout.strip().splitlines()[-1])
-    k, ksrc = oracle_iters_per_step(name, precond)
-    if k is None:
-        k, ksrc = native_iters, "CG iterations per step measured on the GPU in this run"
-    sec_per_dof_step = s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"]
+    sec_per_dof_step = s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (kint + 1) * s["cg_s_per_dof_iter"]
     return {"value": 1e-6 / sec_per_dof_step, "unit": "Mdof·steps/s", "cores": threads, "kind": "oracle",
-            "sample": ("FP64 NumPy oracle, %d thread(s), on a %dx%d-cell grid (n=%d, %d dof): one RHS "
-                       "(bracket + viscous term + AB3 update), the Poisson setup and 5 CG operator "
-                       "applications with the %s preconditioner, timed per dof and scaled to one step "
-                       "of %.0f CG iterations (%s); %.1f s of CPU"
-                       % (threads, SAMPLE_CELLS, SAMPLE_CELLS, wl["n"], s["sample_dof"], precond, k, ksrc,
-                          time.time() - t0)),
+            "sample": ("FP64 NumPy oracle, %d thread(s): %d full AB3 steps (bracket + viscous term + update, "
+                       "Poisson setup, %d CG iterations with the %s preconditioner; %s) on a %dx%d-cell "
+                       "grid of the same n=%d, field and parameters (%d dof), rate per dof; %.1f s of CPU"
+                       % (threads, s["reps"], kint, precond, ksrc, s["cells"], s["cells"], wl["n"],
+                          s["sample_dof"], s["cpu_s"])),
             "parts_s_per_dof": s}
 
 
@@ -261,13 +272,14 @@ def run_reference(args, wl, name):
     k, ksrc = oracle_iters_per_step(name, args.precond)
     if k is None:
         k, ksrc = 30.0, "assumed 30 CG iterations per step (no measured count for this workload)"
+    kint = max(1, int(round(k)))
     for _ in range(args.warmup):
-        oracle_sample(wl, 1, args.precond)
+        oracle_sample(wl, kint, args.precond)
     t0 = time.perf_counter()
     secs = []
     for _ in range(args.steps):
-        s = oracle_sample(wl, 1, args.precond)
-        secs.append(s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (k + 1) * s["cg_s_per_dof_iter"])
+        s = oracle_sample(wl, kint, args.precond)
+        secs.append(s["rhs_s_per_dof"] + s["setup_s_per_dof"] + (kint + 1) * s["cg_s_per_dof_iter"])
     wall = time.perf_counter() - t0
     dof = wl["N"] * wl["N"] * wl["n"] ** 2
     sec_per_step = sum(secs) / len(secs) * dof
@@ -278,9 +290,10 @@ def run_reference(args, wl, name):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(name, wl, "fp64"),
             "cpu_baseline": {"value": value, "unit": "Mdof·steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "each step: oracle RHS + Poisson setup + 2 CG applications on a %dx%d-cell "
-                                       "grid, scaled per dof to %dx%d cells and %.0f CG iterations (%s); %.1f s wall"
-                                       % (SAMPLE_CELLS, SAMPLE_CELLS, wl["N"], wl["N"], k, ksrc, wall)},
+                             "sample": "each step: one full oracle AB3 step (RHS, Poisson setup, %d CG iterations; "
+                                       "%s) on a %dx%d-cell grid of the same n, field and parameters, "
+                                       "rate per dof applied to %dx%d cells; %.1f s wall"
+                                       % (kint, ksrc, SAMPLE_CELLS, SAMPLE_CELLS, wl["N"], wl["N"], wall)},
             "e2e": {"value": value, "unit": "Mdof·steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
