@@ -301,7 +301,7 @@ int dg_sim_set_cg(dg_sim* s, double tol, int maxit, int fixed_iters);
  * residual has fallen by tol_in (0 < tol_in < 1), or by half the factor still missing to the
  * CG tolerance if that is looser; at most max_sweeps >= 1 float64 refinement sweeps per solve
  * (the float64 residual must reach the CG tolerance of dg_sim_create / dg_sim_set_cg).
- * Defaults: tol_in = 3e-4, max_sweeps = 40.
+ * Defaults: tol_in = 1e-4, max_sweeps = 40.
  */
 int dg_sim_set_refinement(dg_sim* s, double tol_in, int max_sweeps);
 

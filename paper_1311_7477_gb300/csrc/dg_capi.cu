@@ -1232,7 +1232,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
   s->tol = cg_tol;
   s->maxit = cg_maxit;
   s->precision = precision;
-  s->tol_in = 3e-4;
+  s->tol_in = 1e-4;
   s->max_sweeps = 40;
   s->p0 = 0;
   s->p1 = 1;
