@@ -341,7 +341,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-steps-scale", type=float, default=0.02)
-    ap.add_argument("--serve-max-cells", type=int, default=1024)
+    ap.add_argument("--serve-max-cells", type=int, default=512)
     ap.add_argument("--serve-groups", type=int, default=0, help="block groups of the batch (0: automatic)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
@@ -738,7 +738,7 @@ def run_batch(args):
 
 def run_serve(args):
     """The served workload: Poisson arrivals at 20 requests/s (seed 7), cells per side in
-    {64,...,1024} (powers of two), n in {3,4,5}, D log-uniform, random-phase or shear-layer
+    {64,...,--serve-max-cells} (powers of two; 512 by default), n in {3,4,5}, D log-uniform, random-phase or shear-layer
     fields; step counts U{100..2000} scaled by --serve-steps-scale (the unscaled trace is about
     an hour of GPU work)."""
     import torch
@@ -776,7 +776,7 @@ def run_serve(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "serve", "requests": len(trace), "rate_per_s": 20, "cells": list(Ns),
                        "n": [3, 4, 5], "steps_scale": args.serve_steps_scale, "groups": args.serve_groups,
-                       "precision": {0: "fp64", 1: "mixed", 2: "mixed64"}[prec], "cg_preconditioner": args.precond},
+                       "precision": {0: "fp64", 1: "mixed", 2: "mixed64", 3: "fp64pc32"}[prec], "cg_preconditioner": args.precond},
             "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
             "served": rep, "field_generation_s_before_clock": t_gen}
     print(json.dumps(line))

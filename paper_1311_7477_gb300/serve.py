@@ -166,6 +166,7 @@ class Server:
         queue = []
         inflight = []          # (event, requests whose last step is in that launch)
         self.graveyard = []
+        self.failed = []
         self.nodes = {}
         self.pool = ThreadPoolExecutor(max_workers=4)
         t0 = clock()
@@ -195,7 +196,15 @@ class Server:
                     if self.used + need > self.budget and self.active:
                         break
                     queue.pop(0)
-                    self._admit(r, clock() - t0, clock)
+                    try:
+                        self._admit(r, clock() - t0, clock)
+                    except dg.DGError as e:
+                        # a start-up failure (e.g. the initial Poisson solve not converging)
+                        # ends this request with its error; the others carry on
+                        r.field = None
+                        self.failed.append({"id": r.id, "N": r.spec["N"], "n": r.spec["n"],
+                                            "error": str(e)})
+                        continue
                     admitted = True
                 if self.graveyard and admitted:
                     self._bury()   # the admission has synchronised the device: frees do not stall
@@ -238,7 +247,8 @@ class Server:
         wall = clock() - t0
         lat = np.array([r.done_t - r.arrival * time_scale for r in self.done])
         st = self.batch.status(check=False)
-        return {"requests": len(self.done), "wall_s": wall,
+        return {"requests": len(self.done), "failed": len(self.failed), "failures": self.failed[:8],
+                "wall_s": wall,
                 "mdof_steps_per_s": self.dof_steps / wall / 1e6,
                 "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
