@@ -44,3 +44,22 @@ def test_served_results_equal_alone(dg, precision):
         ew = np.linalg.norm(om.cpu().numpy() - wb) / np.linalg.norm(wb)
         ep = np.linalg.norm(ps.cpu().numpy() - pb) / np.linalg.norm(pb)
         assert ew < 1e-9 and ep < 1e-9, (spec, ew, ep)
+
+
+def test_failed_request_does_not_stop_the_others(dg):
+    """A request whose start-up solve fails (here: a non-finite initial field) ends with its
+    error in the report; the other requests are served as usual."""
+    from paper_1311_7477_gb300 import serve, workloads
+    trace = workloads.request_trace(count=4, rate=400.0, seed=13, Ns=(16, 24), ns=(2, 3), steps=(3, 8))
+    bad = trace[1]
+    g = dg.Grid(bad["N"], bad["N"], bad["n"])
+    w = np.zeros(g.shape)
+    w[0, 0, 0, 0] = np.nan
+    bad["omega0"] = w
+    g.close()
+    srv = serve.Server(max_active=4, hbm_budget=1e9, precision=dg.DG_MIXED64, precond="twolevel", cg_tol=1e-10,
+                       chunk=3)
+    rep = srv.run(trace)
+    assert rep["failed"] == 1 and rep["failures"][0]["id"] == bad["id"], rep["failures"]
+    assert rep["requests"] == len(trace) - 1 and rep["batch_status"] == 0
+    assert sorted(r.id for r in srv.done) == sorted(s["id"] for s in trace if s is not bad)
