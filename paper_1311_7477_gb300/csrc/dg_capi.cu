@@ -1,53 +1,13 @@
 // The C ABI of libdgk (include/dg.h): handles, argument checks, operator tables, kernel
 // launches and the time-stepper orchestration.  No function here aborts or prints; errors
 // are returned as DG_ERR_* with a thread-local message.
-#include <cuda_runtime.h>
+#include "dg_host.cuh"
 
-#include <algorithm>
-#include <cmath>
-#include <cstdarg>
-#include <cstdint>
-#include <cstdio>
-#include <cstring>
-#include <new>
-#include <type_traits>
-#include <mutex>
-#include <vector>
-
-#include "../../include/dg.h"
-#include "dg_kernels.cuh"
-#include "dg_tables.h"
-
-using namespace dgk;
+namespace dgk {
+thread_local char g_err[512] = "";
+}  // namespace dgk
 
 namespace {
-
-thread_local char g_err[512] = "";
-
-int fail(int code, const char* fmt, ...) {
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(g_err, sizeof(g_err), fmt, ap);
-  va_end(ap);
-  return code;
-}
-
-#define CUDA_TRY(expr)                                                                     \
-  do {                                                                                     \
-    cudaError_t e_ = (expr);                                                               \
-    if (e_ != cudaSuccess) return fail(e_ == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA, \
-                                       "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
-  } while (0)
-
-inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
-
-// Host copies of the device operator tables for one n, in float64 and float32.
-struct OpsHost {
-  alignas(16) unsigned char d[sizeof(Ops2D<double, kMaxN>)];
-  alignas(16) unsigned char f[sizeof(Ops2D<float, kMaxN>)];
-};
 
 template <typename T, int N>
 void fill_op(Op1D<T, N>& o, const double M[kMaxN][kMaxN], const double* a, const double* r, const double* d,
@@ -116,133 +76,7 @@ Ops2D<T, N> make_ops(const RefTables& t, double hx, double hy) {
   return O;
 }
 
-template <int N>
-NodeWeights<N> make_weights(const RefTables& t, double hx, double hy) {
-  NodeWeights<N> W;
-  for (int a = 0; a < N; ++a)
-    for (int b = 0; b < N; ++b) {
-      const double w = (hy * 0.5 * t.w[a]) * (hx * 0.5 * t.w[b]);
-      W.w[a * N + b] = w;
-      W.sw[a * N + b] = std::sqrt(w);
-      W.isw[a * N + b] = 1.0 / std::sqrt(w);
-    }
-  return W;
-}
-
-// Built-in tiles (cells per block, TY x TX) for the RHS kernel and the CG kernel.
-void default_tiles(int n, int& rty, int& rtx, int& cty, int& ctx) {
-  static const int R[6][2] = {{0, 0}, {16, 16}, {8, 16}, {8, 8}, {4, 8}, {4, 8}};
-  static const int Cg[6][2] = {{0, 0}, {16, 16}, {16, 16}, {8, 16}, {8, 8}, {8, 8}};
-  rty = R[n][0];
-  rtx = R[n][1];
-  cty = Cg[n][0];
-  ctx = Cg[n][1];
-}
-
-// Small grids: halve the larger tile side until the grid has at least one tile per SM (or
-// the tile is down to 4 cells), so that the few cells are spread over many blocks -- the
-// solves' phases are then short chains of work rather than long loops in a few blocks.
-void fit_tile(int Nx, int Ny, int sms, int& ty, int& tx) {
-  auto tiles = [&]() { return (long long)((Nx + tx - 1) / tx) * ((Ny + ty - 1) / ty); };
-  while (tiles() < sms && ty * tx > 4) {
-    if (tx >= ty && tx > 1)
-      tx /= 2;
-    else if (ty > 1)
-      ty /= 2;
-    else
-      break;
-  }
-}
-
-void choose_tiles(int n, int Nx, int Ny, int sms, int& rty, int& rtx, int& cty, int& ctx) {
-  default_tiles(n, rty, rtx, cty, ctx);
-  // a single simulation's RHS kernel at n = 5 is faster on 8 x 8 tiles (1024^2 cells:
-  // 5.5 against 6.6 ms per bracket), whose ~200 KB of shared memory a batch, sizing its
-  // kernel for every member, would pay in resident blocks: batches keep 4 x 8
-  if (n == 5) rty = 8;
-  fit_tile(Nx, Ny, sms, rty, rtx);
-  fit_tile(Nx, Ny, sms, cty, ctx);
-}
-
 }  // namespace
-
-// ---------------------------------------------------------------------------------------
-// Handles
-// ---------------------------------------------------------------------------------------
-
-struct Workspace {
-  size_t ndof = 0;
-  int grid_cap = 0;  // capacity of the partials (blocks)
-  double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *y = nullptr;
-  double* part = nullptr;  // 4 * grid_cap
-  // float32 inner-solve vectors of the mixed precision path
-  float *rf = nullptr, *fr = nullptr, *fe = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fq = nullptr;
-  float* partf = nullptr;
-  // two-level preconditioner work arrays (float64 and, for the mixed path, float32)
-  double *pz = nullptr, *prc = nullptr, *puc = nullptr;
-  Cplx<double>* pC = nullptr;
-  float *pzf = nullptr, *prcf = nullptr, *pucf = nullptr;
-  Cplx<float>* pCf = nullptr;
-  SyncState* sync = nullptr;
-  SolveStatus* status = nullptr;
-  double* inv_part = nullptr;  // 3 * kInvBlocks
-  double* inv_out = nullptr;   // 3
-  double* host_out = nullptr;  // pinned 3
-};
-
-constexpr int kInvBlocks = 1024;
-
-// Device tables of the two-level preconditioner (see PrecondArgs), float64 and float32.
-struct PcTables {
-  double* Bt = nullptr;
-  Cplx<double>*twx = nullptr, *twy = nullptr;
-  double *ax = nullptr, *ay = nullptr;
-  float* Btf = nullptr;
-  Cplx<float>*twxf = nullptr, *twyf = nullptr;
-  float *axf = nullptr, *ayf = nullptr;
-  int log2x = -1, log2y = -1;
-};
-
-struct dg_grid {
-  int Nx, Ny, n;
-  double Lx, Ly, hx, hy, tau;
-  RefTables rt;
-  int rTY, rTX, cTY, cTX;
-  int num_sms;
-  OpsHost ops;
-  Workspace ws;
-  int precond = 0;  // DG_PRECOND_JACOBI or DG_PRECOND_TWOLEVEL
-  bool cluster_ok = true;  // small solves may run as one thread-block cluster
-  PcTables pc;
-  void* d_opsd = nullptr;  // device copies of the operator tables (batched kernel)
-  void* d_opsf = nullptr;
-};
-
-struct dg_sim {
-  dg_grid* g;
-  long long batch_limit = 0;  // batched steps stop at this step index (0: no limit)
-  double D, dt, tol;
-  int precision, maxit, fixed_iters;
-  long long step;
-  double* omega[2];
-  int oc;
-  double* psi[3];  // scaled: sqrt(W) psi
-  int p0, p1, p2;
-  void* R[4];      // history ring: float64 (DG_FP64) or float32 (DG_MIXED)
-  int r1, r2, r3, rfree;  // R^{k-1}, R^{k-2}, R^{k-3}, free slot
-  int K = 3;              // steps of the Adams-Bashforth method (1..4)
-  int parts = 0;          // bracket parts (0: J of Eq. J; 1: J++ alone, the naive bracket)
-  double *stA, *stB;  // RK stage vorticities
-  void *k2, *k3;      // RK stage slopes (same type as R)
-  double tol_in;      // inner relative tolerance of the float32 sweeps (DG_MIXED)
-  int max_sweeps;
-  Workspace ws;
-  // launch accounting / device timing
-  long long launches = 0, rhs_launches = 0, cg_launches = 0;
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_rhs, ev_cg;  // start/stop pairs
-  size_t n_ev_rhs = 0, n_ev_cg = 0;
-};
 
 namespace {
 
@@ -322,47 +156,10 @@ int alloc_ws_mixed(Workspace& w) {
   return DG_OK;
 }
 
-size_t ndof_of(const dg_grid* g) { return (size_t)g->Nx * g->Ny * g->n * g->n; }
-
-Geom geom_of(const dg_grid* g, int TY, int TX) {
-  Geom G;
-  G.Nx = g->Nx;
-  G.Ny = g->Ny;
-  G.TY = std::min(TY, g->Ny);
-  G.TX = std::min(TX, g->Nx);
-  G.tilesX = (g->Nx + G.TX - 1) / G.TX;
-  G.tilesY = (g->Ny + G.TY - 1) / G.TY;
-  return G;
-}
-
-template <typename T, int N>
-const Ops2D<T, N>& ops_of(const dg_grid* g) {
-  if constexpr (sizeof(T) == 8) return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.d);
-  else return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.f);
-}
-
 template <int N>
 void build_ops(dg_grid* g) {
   new (g->ops.d) Ops2D<double, N>(make_ops<double, N>(g->rt, g->hx, g->hy));
   new (g->ops.f) Ops2D<float, N>(make_ops<float, N>(g->rt, g->hx, g->hy));
-}
-
-template <class F>
-int dispatch_n(int n, F&& f) {
-  switch (n) {
-    case 1: return f(std::integral_constant<int, 1>{});
-    case 2: return f(std::integral_constant<int, 2>{});
-    case 3: return f(std::integral_constant<int, 3>{});
-    case 4: return f(std::integral_constant<int, 4>{});
-    case 5: return f(std::integral_constant<int, 5>{});
-  }
-  return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
-}
-
-template <typename Kern>
-int set_smem(Kern k, size_t bytes) {
-  if (bytes > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return DG_OK;
 }
 
 // ---- two-level preconditioner tables ---------------------------------------------------
@@ -501,211 +298,6 @@ int upload_ops(dg_grid* g) {
   return DG_OK;
 }
 
-PrecondArgs<double> pc_args(const dg_grid* g, const Workspace& w) {
-  PrecondArgs<double> P{};
-  P.Bt = g->pc.Bt;
-  P.twx = g->pc.twx;
-  P.twy = g->pc.twy;
-  P.ax = g->pc.ax;
-  P.ay = g->pc.ay;
-  P.log2x = g->pc.log2x;
-  P.log2y = g->pc.log2y;
-  P.z = w.pz;
-  P.rc = w.prc;
-  P.uc = w.puc;
-  P.C = w.pC;
-  return P;
-}
-
-PrecondArgs<float> pc_args_f(const dg_grid* g, const Workspace& w) {
-  PrecondArgs<float> P{};
-  P.Bt = g->pc.Btf;
-  P.twx = g->pc.twxf;
-  P.twy = g->pc.twyf;
-  P.ax = g->pc.axf;
-  P.ay = g->pc.ayf;
-  P.log2x = g->pc.log2x;
-  P.log2y = g->pc.log2y;
-  P.z = w.pzf;
-  P.rc = w.prcf;
-  P.uc = w.pucf;
-  P.C = w.pCf;
-  return P;
-}
-
-// ---- launches ---------------------------------------------------------------------------
-
-template <typename T, int N>
-int launch_rhs(const dg_grid* g, const RhsArgs<T>& A, cudaStream_t st) {
-  const Geom G = geom_of(g, g->rTY, g->rTX);
-  const size_t smem = table_bytes<Ops2D<T, N>>() + rhs_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
-  if (int rc = set_smem(rhs_kernel<T, N>, smem)) return rc;
-  rhs_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, A);
-  CUDA_TRY(cudaGetLastError());
-  return DG_OK;
-}
-
-template <typename T, int N>
-int launch_apply(const dg_grid* g, const double* x, double* y, int mode, cudaStream_t st) {
-  const Geom G = geom_of(g, g->cTY, g->cTX);
-  const size_t smem = table_bytes<Ops2D<T, N>>() + apply_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
-  if (int rc = set_smem(apply_kernel<T, N>, smem)) return rc;
-  apply_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, x, y, mode);
-  CUDA_TRY(cudaGetLastError());
-  return DG_OK;
-}
-
-// Cooperative launch of the persistent CG kernel: as many blocks as can be co-resident
-// (capped by the number of tiles and the partials capacity).
-// Records the next event of a start/stop pool (growing it as needed).
-int record_event(std::vector<cudaEvent_t>& pool, size_t& used, cudaStream_t st) {
-  if (used == pool.size()) {
-    cudaEvent_t e;
-    CUDA_TRY(cudaEventCreate(&e));
-    pool.push_back(e);
-  }
-  CUDA_TRY(cudaEventRecord(pool[used++], st));
-  return DG_OK;
-}
-
-// Small grids: if the built-in tiles of n cover the grid with at most kClusterMax tiles, the
-// mixed-precision solve (float32 inner iterations: latency-bound, not throughput-bound) runs
-// as ONE thread-block cluster of that many blocks, whose phases meet at the hardware cluster
-// barrier instead of the grid barrier in global memory.  The float64 solve, bound by the
-// float64 FMA rate, keeps the whole GPU (small tiles, cooperative launch): on 32^2 cells, n = 3,
-// a cluster of 8 blocks took 66 us per float64 iteration against 46 us on 256 tiles, while
-// the mixed solve ran twice as fast as a cluster.
-constexpr int kClusterMax = 8;  // the portable cluster size
-
-Geom solve_geom(const dg_grid* g, bool allow_cluster, bool* cluster) {
-  int rty, rtx, cty, ctx;
-  default_tiles(g->n, rty, rtx, cty, ctx);
-  const Geom Gd = geom_of(g, cty, ctx);
-  *cluster = allow_cluster && g->cluster_ok && Gd.tilesX * Gd.tilesY <= kClusterMax;
-  return *cluster ? Gd : geom_of(g, g->cTY, g->cTX);
-}
-
-// Launches kern with args on grid blocks: as one cluster (cluster == true; cooperative
-// launch otherwise).  Returns false in *launched when the cluster does not fit (the caller
-// then falls back to a cooperative launch).
-template <class Kern, class... Args>
-int launch_solve(Kern kern, bool cluster, int grid, size_t smem, cudaStream_t st, bool* launched, Args... args) {
-  *launched = false;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  if (cluster) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = grid;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      return DG_OK;
-    }
-  } else {
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-  CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args...));
-  *launched = true;
-  return DG_OK;
-}
-
-template <typename T, int N, typename TP = T>
-int launch_cg(const dg_grid* g, CgArgs<T, TP> A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
-  bool cluster = false;
-  Geom G = solve_geom(g, false, &cluster);
-  size_t smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
-  auto kern = cg_kernel<T, N, TP>;
-  if (int rc = set_smem(kern, smem)) return rc;
-  int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-  if (per_sm < 1) return fail(DG_ERR_CUDA, "CG kernel does not fit on an SM (smem %zu B)", smem);
-  int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
-  grid = std::min(grid, w.grid_cap);
-  A.part = reinterpret_cast<T*>(w.part);
-  A.sync = w.sync;
-  A.status = w.status;
-  if constexpr (std::is_same<TP, double>::value)
-    A.pc = pc_args(g, w);
-  else
-    A.pc = pc_args_f(g, w);
-  CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
-  const bool tm = timed && timed->timing;
-  if (tm)
-    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
-  bool launched = false;
-  A.cluster = cluster ? 1 : 0;
-  if (int rc = launch_solve(kern, cluster, grid, smem, st, &launched, ops_of<T, N>(g), G, A)) return rc;
-  if (!launched) {  // no room for the cluster: the tiles of a cooperative launch instead
-    G = geom_of(g, g->cTY, g->cTX);
-    smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
-    if (int rc = set_smem(kern, smem)) return rc;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    grid = std::min({per_sm * g->num_sms, G.tilesX * G.tilesY, w.grid_cap});
-    A.cluster = 0;
-    if (int rc = launch_solve(kern, false, grid, smem, st, &launched, ops_of<T, N>(g), G, A)) return rc;
-  }
-  if (tm)
-    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
-  return DG_OK;
-}
-
-template <int N>
-int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t st, dg_sim* timed = nullptr) {
-  bool cluster = false;
-  Geom G = solve_geom(g, true, &cluster);
-  auto smem_of = [&](const Geom& Gx) {
-    return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>() +
-           mixed_smem_bytes<N>(Gx.TY, Gx.TX, std::max(g->Nx, g->Ny), A.precond == 1);
-  };
-  size_t smem = smem_of(G);
-  auto kern = mixed_cg_kernel<N>;
-  if (int rc = set_smem(kern, smem)) return rc;
-  int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-  if (per_sm < 1) return fail(DG_ERR_CUDA, "mixed CG kernel does not fit on an SM (smem %zu B)", smem);
-  int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
-  grid = std::min(grid, w.grid_cap);
-  A.rf = w.rf;
-  A.v = CgVectors<float>{w.fe, w.fr, w.fp0, w.fp1, w.fq};
-  A.pc = pc_args_f(g, w);
-  A.partd = w.part;
-  A.partf = w.partf;
-  A.sync = w.sync;
-  A.status = w.status;
-  CUDA_TRY(cudaMemsetAsync(w.sync, 0, sizeof(SyncState), st));
-  const bool tm = timed && timed->timing;
-  if (tm)
-    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
-  bool launched = false;
-  A.cluster = cluster ? 1 : 0;
-  if (int rc = launch_solve(kern, cluster, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), G, A))
-    return rc;
-  if (!launched) {  // no room for the cluster: the tiles of a cooperative launch instead
-    G = geom_of(g, g->cTY, g->cTX);
-    smem = smem_of(G);
-    if (int rc = set_smem(kern, smem)) return rc;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    grid = std::min({per_sm * g->num_sms, G.tilesX * G.tilesY, w.grid_cap});
-    A.cluster = 0;
-    if (int rc = launch_solve(kern, false, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), G, A))
-      return rc;
-  }
-  if (tm)
-    if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
-  return DG_OK;
-}
-
 int read_status(const Workspace& w, SolveStatus* out, cudaStream_t st) {
   CUDA_TRY(cudaMemcpyAsync(out, w.status, sizeof(SolveStatus), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -719,18 +311,6 @@ int flags_to_status(int flags) {
   return DG_OK;
 }
 
-template <int N>
-int launch_invariants(const dg_grid* g, const double* psi, const double* omega, int psi_scaled, const Workspace& w,
-                      cudaStream_t st) {
-  const NodeWeights<N> W = make_weights<N>(g->rt, g->hx, g->hy);
-  const size_t nd = ndof_of(g);
-  const int blocks = (int)std::min<size_t>(kInvBlocks, (nd + kThreads - 1) / kThreads);
-  invariants_partial_kernel<N><<<blocks, kThreads, 0, st>>>(W, psi, omega, nd, psi_scaled, w.inv_part);
-  invariants_final_kernel<<<1, 32, 0, st>>>(w.inv_part, blocks, w.inv_out);
-  CUDA_TRY(cudaGetLastError());
-  return DG_OK;
-}
-
 int finish_invariants(const Workspace& w, double out[3], cudaStream_t st) {
   CUDA_TRY(cudaMemcpyAsync(w.host_out, w.inv_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -739,8 +319,6 @@ int finish_invariants(const Workspace& w, double out[3], cudaStream_t st) {
     if (!std::isfinite(out[j])) return fail(DG_ERR_NONFINITE, "invariant %d is not finite", j);
   return DG_OK;
 }
-
-int co_resident_cap(const dg_grid* g) { return std::max(64, 8 * g->num_sms); }
 
 }  // namespace
 
@@ -762,8 +340,7 @@ int dg_selftest_wait_cap(void* stream) {
   CUDA_TRY(cudaMalloc(&out, sizeof(int)));
   CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(SyncState), st));
   CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int), st));
-  void* args[] = {(void*)&s, (void*)&out};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(4), dim3(64), args, 0, st);
+  cudaError_t e = launch_barrier_selftest(s, out, st);
   int flags = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, out, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1162,10 +739,7 @@ int sim_ab3_step(dg_sim* s, cudaStream_t st) {
 int R_to_double(const dg_sim* s, const void* R, double* dst, cudaStream_t st) {
   const size_t nd = ndof_of(s->g);
   if (s->precision == DG_MIXED) {
-    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
-    convert_kernel<float, double><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(R), dst, nd);
-    CUDA_TRY(cudaGetLastError());
-    return DG_OK;
+    return launch_convert_f2d(static_cast<const float*>(R), dst, nd, st);
   }
   CUDA_TRY(cudaMemcpyAsync(dst, R, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return DG_OK;
@@ -1174,25 +748,14 @@ int R_to_double(const dg_sim* s, const void* R, double* dst, cudaStream_t st) {
 int R_from_double(const dg_sim* s, const double* src, void* R, cudaStream_t st) {
   const size_t nd = ndof_of(s->g);
   if (s->precision == DG_MIXED) {
-    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
-    convert_kernel<double, float><<<blocks, kThreads, 0, st>>>(src, static_cast<float*>(R), nd);
-    CUDA_TRY(cudaGetLastError());
-    return DG_OK;
+    return launch_convert_d2f(src, static_cast<float*>(R), nd, st);
   }
   CUDA_TRY(cudaMemcpyAsync(R, src, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return DG_OK;
 }
 
 int scale_field(const dg_grid* g, const double* x, double* y, int inverse, cudaStream_t st) {
-  return dispatch_n(g->n, [&](auto nc) {
-    constexpr int N = decltype(nc)::value;
-    const NodeWeights<N> W = make_weights<N>(g->rt, g->hx, g->hy);
-    const size_t nd = ndof_of(g);
-    const int blocks = (int)std::min<size_t>(4096, (nd + kThreads - 1) / kThreads);
-    scale_nodes_kernel<N><<<blocks, kThreads, 0, st>>>(W, x, y, nd, inverse);
-    CUDA_TRY(cudaGetLastError());
-    return DG_OK;
-  });
+  return dispatch_n(g->n, [&](auto nc) { return launch_scale<decltype(nc)::value>(g, x, y, inverse, st); });
 }
 
 }  // namespace
@@ -1827,9 +1390,8 @@ int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (smem > (size_t)optin) return fail(DG_ERR_ARG, "batch needs %zu B of shared memory per block (max %d)", smem, optin);
-  if (int rc = set_smem(batch_kernel, smem)) return rc;
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, smem));
+  if (int rc = batch_kernel_occupancy(smem, &per_sm)) return rc;
   if (per_sm < 1) return fail(DG_ERR_CUDA, "batch kernel does not fit on an SM");
   int grid = per_sm * dev_sms;
   for (dg_sim* s : b->sims) grid = std::min(grid, s->ws.grid_cap);
@@ -1893,19 +1455,7 @@ int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
 int batch_enqueue(dg_batch* b, int nsteps, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, b->ngroups * sizeof(SyncState), st));
   BatchArgs A{b->d_sims, b->d_order, b->d_groups, b->ngroups, nsteps, b->d_error};
-  // cudaLaunchKernelEx with the cooperative attribute: the form of a cooperative launch
-  // that stream capture (and so the CUDA graph) accepts.
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = b->smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  CUDA_TRY(cudaLaunchKernelEx(&cfg, batch_kernel, A));
+  if (int rc = batch_kernel_launch(A, b->grid, b->smem, st)) return rc;
   return DG_OK;
 }
 

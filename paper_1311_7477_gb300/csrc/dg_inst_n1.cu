@@ -1,0 +1,4 @@
+// The kernels and launchers of the hot path for n = 1 nodes per cell and dimension.
+#include "dg_launch.cuh"
+
+DGK_INSTANTIATE_LAUNCHERS(1)

@@ -1221,7 +1221,7 @@ struct BatchArgs {
 };
 
 template <typename T, int N>
-__device__ __forceinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& C, int oc, int p0, int r1, int r2,
+__device__ __noinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& C, int oc, int p0, int r1, int r2,
                                           int rfree, int vrank, int vsize, unsigned char* smem) {
   RhsArgs<T> A{};
   A.psi = S.psi[p0];
@@ -1249,7 +1249,7 @@ __host__ __device__ constexpr size_t batch_ops_bytes() {
 }
 
 template <int N>
-__device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int vrank, unsigned char* smem_all,
+__device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int vrank, unsigned char* smem_all,
                                            double* redd, double* bcd, float* redf, float* bcf, int* s_flag) {
   constexpr int NN = N * N;
   const BatchSim& S = *Sp;
@@ -1350,42 +1350,7 @@ __device__ __forceinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, 
   return grid_barrier(grp.sync, s_flag, grp.nblocks);
 }
 
-__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double redd[32];
-  __shared__ double bcd;
-  __shared__ float redf[32];
-  __shared__ float bcf;
-  __shared__ int s_flag;
-  int gi = 0;
-  while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.groups[gi + 1].first_block) ++gi;
-  const BatchGroup grp = A.groups[gi];
-  const int vrank = int(blockIdx.x) - grp.first_block;
-  bool ok = true;
-  for (int st = 0; st < A.nsteps && ok; ++st) {
-    for (int j = 0; j < grp.count && ok; ++j) {
-      BatchSim* S = A.sims + A.order[grp.first + j];
-      switch (S->n) {
-        case 1: ok = batch_step<1>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
-        case 2: ok = batch_step<2>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
-        case 3: ok = batch_step<3>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
-        case 4: ok = batch_step<4>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
-        case 5: ok = batch_step<5>(S, grp, vrank, smem_raw, redd, &bcd, redf, &bcf, &s_flag); break;
-        default: ok = false;
-      }
-    }
-  }
-  if (!ok && threadIdx.x == 0) atomicCAS(A.error, 0, kFlagTimeout);
-}
 
-// Self-test of the capped grid barrier: block 0 never arrives, so every other block's wait
-// runs out after kSpinCap polls and raises kFlagTimeout; nothing faults or hangs.
-__global__ void barrier_selftest_kernel(SyncState* s, int* out) {
-  __shared__ int f;
-  if (blockIdx.x == 0) return;
-  const bool ok = grid_barrier(s, &f, gridDim.x);
-  if (threadIdx.x == 0 && !ok) atomicOr(out, kFlagTimeout);
-}
 
 // =========================================================================================
 // Invariants: partial sums of W omega, W psi omega, W omega^2 per block, then one block
@@ -1424,13 +1389,6 @@ __global__ void __launch_bounds__(kThreads) invariants_partial_kernel(const __gr
   if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = o;
 }
 
-__global__ void invariants_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
-  __shared__ double bc;
-  for (int j = 0; j < 3; ++j) {
-    const double s = sum_partials(part + j, nparts, 3, &bc);
-    if (threadIdx.x == 0) out[j] = (j == 0) ? s : 0.5 * s;
-  }
-}
 
 // ---- small elementwise kernels ----------------------------------------------------------
 
