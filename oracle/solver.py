@@ -14,6 +14,14 @@ states only that a conjugate gradient method solves it; the details below are a 
   true residual is computed; if that one does not, CG restarts from it (p = W^{-1} r), at
   most MAX_RESTARTS times.  (Over thousands of iterations the recursive residual drifts away
   from the true one by rounding.)
+* the tolerance cannot ask for less than float64 can hold: rounding the exact solution to
+  float64 and evaluating b - A x in float64 leave a residual of up to about
+  2 u lambda_max |W^{1/2} x| in the norm above (u = 2^-53, lambda_max the largest
+  eigenvalue of W^{-1/2} A W^{-1/2}); so the true residual is also accepted once it is below
+  that floor and no longer falls (less than a factor 4 below the previous check), with
+  lambda_max bounded by the operator's row sums (rounding_floor2).  On fine grids with
+  smooth solutions (1024^2 cells, n = 5, a double shear layer) the attainable residual is
+  about 3e-10, above a tolerance of 1e-10.
 
 With x0 of W-mean zero all iterates stay W-mean zero, since every update direction
 z = W^{-1} r satisfies sum W z = sum r = 0.
@@ -31,8 +39,11 @@ from .operators import ldg_matrix_1d
 def poisson_rhs(ops, omega):
     """b = W (omega - mean_W omega).  The mean is evaluated in two passes (the mean of the
     first-pass deviations corrects the first pass), so that b has no rounding-sized component
-    along the constants, the kernel of A."""
+    along the constants, the kernel of A.  With homogeneous Dirichlet boundaries A is
+    definite and b = W omega."""
     W = ops.W2
+    if getattr(ops, "bc", "periodic") == "dirichlet":
+        return W * omega
     sW = float(np.sum(W))
     m1 = float(np.sum(W * omega)) / sW
     m2 = float(np.sum(W * (omega - m1))) / sW
@@ -40,6 +51,22 @@ def poisson_rhs(ops, omega):
 
 
 MAX_RESTARTS = 20
+
+
+def rounding_floor2(ops):
+    """(2^-52 lambda)^2 with lambda the Gershgorin bound (largest absolute row sum) of
+    W^{-1/2} A W^{-1/2} = I (x) A1x^ + A1y^ (x) I, A1^ = w^{-1/2} A1 w^{-1/2} per direction: the
+    squared float64 rounding floor of the relative residual per unit of W x . x."""
+    g = ops.g
+    n = g.n
+    bound = 0.0
+    for h, w in ((g.hx, ops.wx), (g.hy, ops.wy)):
+        # the rows of the middle cell of a periodic 3-cell line (a Dirichlet boundary cell's
+        # rows are smaller: this bounds both)
+        A1 = ldg_matrix_1d(g.t, 3, h, ops.tau)[n:2 * n, :]
+        sw = np.sqrt(np.tile(w, 3))
+        bound += float(np.max(np.sum(np.abs(A1 / np.sqrt(w)[:, None] / sw[None, :]), axis=1)))
+    return (2.0 ** -52 * bound) ** 2
 
 
 class TwoLevel:
@@ -60,6 +87,8 @@ class TwoLevel:
         g = ops.g
         n = g.n
         t = g.t
+        if getattr(ops, "bc", "periodic") != "periodic":
+            raise ValueError("the two-level preconditioner is built for periodic grids")
         A1x = ldg_matrix_1d(t, 3, g.hx, ops.tau)[n:2 * n, n:2 * n]
         A1y = ldg_matrix_1d(t, 3, g.hy, ops.tau)[n:2 * n, n:2 * n]
         Acc = np.kron(np.diag(ops.wy), A1x) + np.kron(A1y, np.diag(ops.wx))   # node index a*n + b
@@ -109,6 +138,8 @@ def pcg(ops, b, x0, tol, maxit, fixed_iters=0, precond=None):
     p = z.copy()
     rz = float(np.sum(r * z))
     rr = float(np.sum(r * r / W))
+    floor2 = rounding_floor2(ops)
+    rr_prev = None      # true residual at the previous check
     it = 0
     restarts = 0
     converged = True
@@ -119,10 +150,13 @@ def pcg(ops, b, x0, tol, maxit, fixed_iters=0, precond=None):
         elif rr <= tol * tol * rho_b:
             r_true = b - ops.A(x)
             rr_true = float(np.sum(r_true * r_true / W))
-            if rr_true <= tol * tol * rho_b or restarts == MAX_RESTARTS:
+            stagnated = (rr_true <= floor2 * float(np.sum(W * x * x)) and rr_prev is not None
+                         and rr_true > 0.25 * rr_prev)
+            if rr_true <= tol * tol * rho_b or stagnated or restarts == MAX_RESTARTS:
                 rr = rr_true
-                converged = rr_true <= tol * tol * rho_b
+                converged = rr_true <= tol * tol * rho_b or stagnated
                 break
+            rr_prev = rr_true
             restarts += 1
             r = r_true
             z = M(r)
@@ -161,12 +195,14 @@ def solve_poisson(ops, omega, x0, tol, maxit, fixed_iters=0, precond=None):
     return pcg(ops, poisson_rhs(ops, omega), x0, tol, maxit, fixed_iters, precond)
 
 
-def solve_poisson_dense(dense, omega_global):
+def solve_poisson_dense(dense, omega_global, bc="periodic"):
     """Tiny-grid direct solve: (A + (W1)(W1)^T) psi = b, whose unique solution is the
-    W-mean-zero solution of A psi = b.  dense = operators.dense_ops_2d(...); arrays in the
-    global node order."""
+    W-mean-zero solution of A psi = b (periodic); A psi = W omega (Dirichlet, A definite).
+    dense = operators.dense_ops_2d(...); arrays in the global node order."""
     A, W = dense["A"], dense["W"]
     w = omega_global.ravel()
+    if bc == "dirichlet":
+        return np.linalg.solve(A, W * w).reshape(omega_global.shape)
     b = W * (w - np.sum(W * w) / np.sum(W))
     M = A + np.outer(W, W)
     return np.linalg.solve(M, b).reshape(omega_global.shape)

@@ -1,12 +1,17 @@
-"""Writes cg_iterations_shear512_n4_<precond>.json: the CG iterations per Poisson solve that
-the FP64 oracle itself takes on the large single-run workload (512 x 512 cells, n = 4,
-double shear layer rho = delta = 0.05, D = 1e-4, dt = 5e-4, CG tol 1e-10; two RK4 start-up
-steps then AB3), with the given preconditioner.  Calls only oracle/ and the input
-generator.  Used to scale the bounded CPU-baseline sample of bench.py (oracle RHS + a few CG
-iterations) to one full time step.
+"""Writes cg_iterations_<workload>_<precond>.json: the CG iterations per Poisson solve that
+the FP64 oracle itself takes on one of the single-run workloads (two RK4 start-up steps,
+then AB3), with the given preconditioner:
 
-    python tests/golden/make_cg_iterations.py [nsteps] [jacobi|twolevel]
-        (twolevel: about half an hour of CPU; jacobi: many hours)
+    shear512_n4    512 x 512 cells, n = 4, double shear layer rho = delta = 0.05, D = 1e-4,
+                   dt = 5e-4, CG tol 1e-10
+    random1024_n5  1024 x 1024 cells, n = 5, random-phase field (seed 1), D = 0, dt = 2e-4,
+                   CG tol 1e-10
+
+Calls only oracle/ and the input generator.  Used to scale the bounded CPU-baseline sample of
+bench.py (oracle RHS + a few CG iterations) to one full time step.
+
+    python tests/golden/make_cg_iterations.py [workload] [nsteps] [jacobi|twolevel]
+        (shear512_n4, twolevel: about half an hour of CPU; random1024_n5: a few hours)
 """
 import json
 import os
@@ -25,12 +30,19 @@ from oracle.tables import Grid  # noqa: E402
 from paper_1311_7477_gb300 import fields  # noqa: E402
 
 
-def main(nsteps=4, precond="twolevel"):
-    N, n, D, dt, tol = 512, 4, 1e-4, 5e-4, 1e-10
+WORKLOADS = {
+    "shear512_n4": (512, 4, 1e-4, 5e-4, 1e-10, "shear layer 512x512 cells, n=4, D=1e-4, dt=5e-4, CG tol 1e-10"),
+    "random1024_n5": (1024, 5, 0.0, 2e-4, 1e-10,
+                      "random phase (seed 1) 1024x1024 cells, n=5, D=0, dt=2e-4, CG tol 1e-10"),
+}
+
+
+def main(workload="shear512_n4", nsteps=4, precond="twolevel"):
+    N, n, D, dt, tol, what = WORKLOADS[workload]
     g = Grid(N, N, n)
     ops = Operators(g)
     X, Y = g.mesh()
-    w0 = fields.shear_layer(X, Y)
+    w0 = fields.shear_layer(X, Y) if workload.startswith("shear") else fields.random_phase(X, Y, seed=1)
     log = []
     orig = S.solve_poisson
 
@@ -51,18 +63,20 @@ def main(nsteps=4, precond="twolevel"):
         per_step.append({"step": k, "kind": "rk4" if k < 2 else "ab3",
                          "solves": log[before:], "seconds": time.time() - t0})
     out = {
-        "workload": "shear layer 512x512 cells, n=4, D=1e-4, dt=5e-4, CG tol 1e-10 (FP64 oracle)",
+        "workload": what + " (FP64 oracle)",
         "preconditioner": precond,
         "initial_solve": log[0],
         "steps": per_step,
         "ab3_iters_mean": float(np.mean([s["solves"][0]["iters"] for s in per_step if s["kind"] == "ab3"]))
         if nsteps > 2 else None,
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cg_iterations_shear512_n4_%s.json" % precond)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "cg_iterations_%s_%s.json" % (workload, precond))
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path)
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 4, sys.argv[2] if len(sys.argv) > 2 else "twolevel")
+    main(sys.argv[1] if len(sys.argv) > 1 else "shear512_n4", int(sys.argv[2]) if len(sys.argv) > 2 else 4,
+         sys.argv[3] if len(sys.argv) > 3 else "twolevel")

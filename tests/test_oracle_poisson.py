@@ -88,3 +88,29 @@ def test_diffusion_conserves_vorticity(n):
     u = np.random.default_rng(2).standard_normal((6, 5, n, n))
     assert abs(ops.integral(ops.laplacian(u))) < 1e-12 * np.abs(ops.laplacian(u)).max()
     assert np.abs(ops.laplacian(np.full_like(u, 2.5))).max() < 1e-11
+
+
+def test_rounding_floor_bounds_the_spectrum_and_the_rounded_solution():
+    """The float64 rounding floor of the stopping rule: its eigenvalue bound is not below the
+    largest eigenvalue of the scaled operator W^-1/2 A W^-1/2 (dense, tiny grids), and the exact
+    solution rounded to float32 -- a stand-in for float64 rounding, 2^29 times larger -- leaves a
+    relative residual within the floor scaled by the same factor."""
+    from oracle.operators import dense_ops_2d, from_global, to_global
+    from oracle.solver import rounding_floor2, solve_poisson_dense
+    for Nx, Ny, n, tau in ((4, 3, 2, 0.0), (3, 4, 3, 0.5), (5, 5, 4, 0.0)):
+        og = Grid(Nx, Ny, n, 1.3, 0.9)
+        ops = Operators(og, tau=tau)
+        d = dense_ops_2d(og, tau)
+        sw = np.sqrt(d["W"])
+        Ahat = d["A"] / sw[:, None] / sw[None, :]
+        lam = np.linalg.eigvalsh(Ahat).max()
+        bound = np.sqrt(rounding_floor2(ops)) * 2.0 ** 52
+        assert bound >= lam * (1 - 1e-12), (bound, lam)
+        w = np.random.default_rng(n).standard_normal(og.zeros().shape)
+        x = from_global(solve_poisson_dense(d, to_global(w)), n)
+        b = poisson_rhs(ops, w)
+        x32 = x.astype(np.float32).astype(np.float64)
+        r = b - ops.A(x32)
+        rel2 = np.sum(r * r / ops.W2) / np.sum(b * b / ops.W2)
+        floor2_32 = rounding_floor2(ops) * 2.0 ** 58 * np.sum(ops.W2 * x32 * x32) / np.sum(b * b / ops.W2)
+        assert rel2 <= floor2_32, (rel2, floor2_32)
