@@ -6,9 +6,10 @@
 
 A step is one time step of the whole hot path: the Arakawa bracket + viscous term + AB3
 update (one fused kernel) and the CG Poisson solve (one persistent cooperative kernel), on
-synthetic fields shaped like the paper's runs.  Default workload (the large single run):
-512 x 512 periodic cells on [0, 2pi]^2, n = 4 nodes per dimension (4.19M dof), double shear
-layer, D = 1e-4, dt = 5e-4, CG tolerance 1e-10, float64.
+synthetic fields shaped like the paper's runs.  Default workload (the largest single run):
+1024 x 1024 periodic cells on [0, 2pi]^2, n = 5 nodes per dimension (26.2M dof), random-phase
+vorticity with E(k) ~ k^4 exp(-(k/6)^2), D = 0, dt = 2e-4, CG tolerance 1e-10; float64 is the
+headline, the mixed-precision modes are timed in the same run with their one-step error.
 
 Prints ONE JSON line on rank 0.  value = dof * steps / device seconds, summed over ranks
 (each rank advances its own replica: the simulations are independent units, no collective is
@@ -40,11 +41,23 @@ WORKLOADS = {
 # Table 1: milliseconds per bracket evaluation at N = 100 on a GeForce GTX 570 and on a Xeon
 # E3-1225 V2 with 4 threads, FP64
 TABLE1_MS = {1: (0.05, 0.08), 2: (0.26, 0.52), 3: (0.71, 3.85), 4: (1.47, 9.08)}
-DEFAULT_WORKLOAD = "shear512_n4"
+DEFAULT_WORKLOAD = "random1024_n5"
 L2_BYTES = 129 * 1024 * 1024
-# FP64 FMA peak of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (unit counts and
-# maximum SM clock; a dependent-chain DFMA microbenchmark measured 1.20 TFLOP/s at ~2.0 GHz).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 and FP32 FMA peaks of a GB300 from the unit counts and the maximum SM clock: 152 SMs x
+# 2 DFMA / 128 FFMA per clock x 2 flop x 2.070 GHz.  profiles/fma_peak_gb300.json holds the
+# measured figures (an FMA-chain microbenchmark with its sampled clocks), used when present.
+FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def fma_peaks():
+    """(fp64 TFLOP/s, fp32 TFLOP/s, source) of the FMA pipes."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fma_peak_gb300.json")) as f:
+            d = json.load(f)
+        return d["fp64_fma_tflops"], d["fp32_fma_tflops"], "measured (profiles/fma_peak_gb300.json)"
+    except (OSError, KeyError, ValueError):
+        return FP64_PEAK_NOMINAL_TFLOPS, FP32_PEAK_NOMINAL_TFLOPS, "nominal: unit counts x 2.070 GHz"
 
 
 def measured_peaks():
@@ -55,21 +68,23 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def measured_traffic(kernel, workload, precision, variant):
-    """DRAM bytes per launch of `kernel` from the ncu capture summarised in
-    profiles/<kernel>_traffic_<workload>.md (None if there is no row for this setup)."""
-    path = os.path.join(ROOT, "profiles", "%s_traffic_%s.md" % (kernel, workload))
+def measured_traffic(kernel, workload, precision, iters_per_launch=None):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload and precision from the
+    ncu capture recorded in profiles/<kernel>_traffic.json, scaled from the capture's CG
+    iterations per launch to iters_per_launch (the traffic of a solve grows with its iteration
+    count; None if there is no record)."""
+    path = os.path.join(ROOT, "profiles", "%s_traffic.json" % kernel)
     try:
-        lines = open(path).read().splitlines()
-    except OSError:
+        rows = json.load(open(path))["captures"]
+    except (OSError, KeyError, ValueError):
         return None
-    for line in lines:
-        cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) == 5 and cells[:3] == [workload, precision, variant]:
-            try:
-                return int(cells[3])
-            except ValueError:
-                return None
+    for r in rows:
+        if r.get("workload") == workload and r.get("precision") == precision:
+            b = float(r["dram_bytes_per_launch"])
+            k = r.get("iters_per_launch")
+            if iters_per_launch and k:
+                b *= (iters_per_launch + 1.0) / (k + 1.0)   # setup ~ one iteration's traffic
+            return b
     return None
 
 
@@ -333,7 +348,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed64", "fp64pc32"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64", "fp64pc32"],
+                    help="default: fp64 for the single runs, mixed for batch64 and serve")
     ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel"])
     ap.add_argument("--no-mixed-compare", action="store_true")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -343,7 +359,11 @@ def main():
     ap.add_argument("--serve-steps-scale", type=float, default=0.02)
     ap.add_argument("--serve-max-cells", type=int, default=512)
     ap.add_argument("--serve-groups", type=int, default=0, help="block groups of the batch (0: automatic)")
+    ap.add_argument("--batch-compare-fp64", action="store_true",
+                    help="batch64: also run the ensemble in float64 and compare each member")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload in ("batch64", "serve") else "fp64"
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, args.workload)
@@ -434,39 +454,32 @@ def main():
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
 
-    # --- mixed precision: error of one step against the float64 path from the identical state
-    err_vs_fp64 = None
-    if precision != dg.DG_FP64:
-        st = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
-        kk = sim.get_state(*st)
-        ref = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=dg.DG_FP64, cg_tol=wl["tol"], cg_maxit=200000)
-        ref.set_state(kk, *st)
-        sim.set_state(kk, *st)
-        ref.step(1)
-        sim.step(1)
-        wa, pa = torch.empty_like(st[0]), torch.empty_like(st[0])
-        wb, pb = torch.empty_like(st[0]), torch.empty_like(st[0])
-        ref.get(wa, pa)
-        sim.get(wb, pb)
-        torch.cuda.synchronize()
-        err_vs_fp64 = {"omega_rel_l2": float(torch.linalg.norm(wa - wb) / torch.linalg.norm(wa)),
-                       "psi_rel_l2": float(torch.linalg.norm(pa - pb) / torch.linalg.norm(pa)),
-                       "what": "one step from the identical state, mixed vs the float64 path (which matches "
-                               "the FP64 oracle to 1e-12 per step)",
-                       "refine_sweeps_last": int(sim.status().refine_sweeps_last)}
-        ref.close()
-
-    # --- the same workload in the mixed-precision modes (timed the same way), and their
-    # one-step error against the float64 path from the identical state
+    # --- the precision modes on the same workload: each timed like the headline, with its
+    # one-step error from the identical state against the float64 path (which the full-size
+    # parity tests pin to the FP64 oracle at 1e-12 per step on this configuration)
     modes = None
-    if precision == dg.DG_FP64 and not args.no_mixed_compare:
+    fp64_peak, fp32_peak, fma_src = fma_peaks()
+    peaks, peak_src = measured_peaks()
+    if not args.no_mixed_compare:
         modes = {}
         st = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(5)]
         kk = sim.get_state(*st)
         ref_w, ref_p = torch.empty_like(st[0]), torch.empty_like(st[0])
-        sim.step(1)
-        sim.get(ref_w, ref_p)
-        for mname, mprec in (("fp64pc32", dg.DG_FP64_PC32), ("mixed64", dg.DG_MIXED64), ("mixed", dg.DG_MIXED)):
+        ref = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=dg.DG_FP64, cg_tol=wl["tol"], cg_maxit=200000)
+        ref.set_state(kk, *st)
+        ref.step(1)
+        ref.get(ref_w, ref_p)
+        ref.close()
+        what = {"fp64": "float64 throughout (the headline path)",
+                "fp64pc32": "float64 throughout except the CG preconditioner (cell block solve and coarse DFT "
+                            "solve), applied in float32",
+                "mixed64": "float64 bracket/viscous term/update, float32 inner PCG, float64 refinement residual",
+                "mixed": "bracket and viscous term in double-float on the float32 pipe, float32 inner PCG, "
+                         "float64 update and refinement residual"}
+        for mname, mprec in (("fp64", dg.DG_FP64), ("fp64pc32", dg.DG_FP64_PC32), ("mixed64", dg.DG_MIXED64),
+                             ("mixed", dg.DG_MIXED)):
+            if mname == args.precision:
+                continue
             ms_ = dg.Sim(g, st[0], D=wl["D"], dt=wl["dt"], precision=mprec, cg_tol=wl["tol"], cg_maxit=200000)
             ms_.set_state(kk, *st)
             ms_.step(1)
@@ -474,9 +487,12 @@ def main():
             ms_.get(w1, p1)
             torch.cuda.synchronize()
             err = {"omega_rel_l2": float(torch.linalg.norm(w1 - ref_w) / torch.linalg.norm(ref_w)),
-                   "psi_rel_l2": float(torch.linalg.norm(p1 - ref_p) / torch.linalg.norm(ref_p))}
+                   "psi_rel_l2": float(torch.linalg.norm(p1 - ref_p) / torch.linalg.norm(ref_p)),
+                   "psi_relres": float(ms_.status().cg_relres_last)}
+            del w1, p1
             ms_.step(max(args.warmup - 1, 1))
             i0 = ms_.status().cg_iters_total
+            ms_.set_timing(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -485,16 +501,26 @@ def main():
             torch.cuda.synchronize()
             mms = e0.elapsed_time(e1)
             info = ms_.status()
-            modes[mname] = {"value": dof * args.steps * world / (mms / 1e3) / 1e6, "unit": "Mdof·steps/s",
-                            "ms_per_step": mms / args.steps,
-                            "inner_cg_iters_per_step": (info.cg_iters_total - i0) / args.steps,
-                            "refine_sweeps_last": int(info.refine_sweeps_last),
-                            "error_vs_fp64_one_step": err,
-                            "what": {"fp64pc32": "float64 throughout except the CG preconditioner (cell block "
-                                                 "solve and coarse DFT solve), applied in float32",
-                                     "mixed64": "float64 bracket/viscous term/update, float32 inner CG, "
-                                                "float64 refinement residual",
-                                     "mixed": "float32 bracket and inner CG, float64 update and refinement"}[mname]}
+            c = ms_.counters()
+            k_in = (info.cg_iters_total - i0) / args.steps
+            sol_ms = c.cg_ms / max(c.cg_launches, 1)
+            entry = {"value": whole_job_rate(dof, args.steps, world, mms / 1e3), "unit": "Mdof·steps/s",
+                     "ms_per_step": mms / args.steps, "rhs_ms": c.rhs_ms / max(c.rhs_launches, 1),
+                     "solve_ms": sol_ms, "cg_iters_per_step": k_in,
+                     "refine_sweeps_last": int(info.refine_sweeps_last),
+                     "error_vs_fp64_one_step": err, "what": what[mname]}
+            if mprec in (dg.DG_MIXED, dg.DG_MIXED64):
+                # the refinement solve's algorithmic bytes per dof: extrapolation setup 16, each
+                # float64 residual sweep 32 (y, omega in; residual out), each float32 inner
+                # iteration 32 (e, r, p read and written, q written and read: 8 x 4 B)
+                sweeps = max(int(info.refine_sweeps_last), 1)
+                byts = dof * (16 + 32 * (sweeps + 1) + 32 * k_in)
+                gbs = byts / (sol_ms / 1e3) / 1e9
+                entry["roofline"] = {"kernel": "mixed_cg_kernel", "bound": "hbm", "achieved": gbs,
+                                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                                     "peak_source": peak_src,
+                                     "bytes_per_dof": "16 + 32 (sweeps + 1) + 32 x inner iterations"}
+            modes[mname] = entry
             ms_.close()
 
     if rank != 0:
@@ -503,36 +529,48 @@ def main():
         return
 
     value = whole_job_rate(dof, args.steps, world, ms / 1e3)
-    peaks, peak_src = measured_peaks()
     # roofline of the dominant kernel (the persistent CG solve), from its live event timing
     cg_ms_per_launch = cnt.cg_ms / max(cnt.cg_launches, 1)
     rhs_ms_per_launch = cnt.rhs_ms / max(cnt.rhs_launches, 1)
     it_per_launch = (info1.cg_iters_total - info0.cg_iters_total) / max(cnt.cg_launches, 1)
-    # algorithmic work per dof and CG iteration: the operator Ahat with rank-one face coupling
-    # (2 directions x (n + 4) FMA), 5 vector updates / dot products; with the two-level
-    # preconditioner also the cell block solve (n^2 FMA), restriction and prolongation (2 FMA)
-    # and the coarse DFT (4 one-dimensional passes of 5 log2(N) flop per cell, per dof / n^2)
+    # the method's count per dof: a CG iteration is one operator apply (8(n+4)+4 flop with the
+    # derivatives applied as matrix-free 1D operators) and the vector work (10 flop), and moves
+    # x, r, p (read and written) and q (written and read): 64 B in float64; the setup is one
+    # apply and 4 flop, 48 B (three vectors read, three written)
     import math
-    flops_iter = 4 * (n + 4) + 10
-    bytes_iter = 8 * 8                 # x, r, p read+write; q write+read (float64)
+    s8 = 8
+    flops_iter_m = 8 * (n + 4) + 14
+    flops_setup_m = 8 * (n + 4) + 4
+    bytes_iter_m, bytes_setup_m = 8 * s8, 6 * s8
+    # this implementation's count: the assembled 1D operator (2 directions x (n + 4) FMA), the
+    # vector updates and dot products, and the two-level preconditioner (cell block solve n^2
+    # FMA, restriction and prolongation, the coarse DFT: 4 passes of 5 log2(N) flop per cell)
+    flops_iter_i = 4 * (n + 4) + 10
+    bytes_iter_i = 8 * 8
     if args.precond == "twolevel":
-        flops_iter += 2 * n * n + 4 + 2 + 4 * 5 * math.log2(N) / (n * n)
-        bytes_iter += 2 * 8            # z written and read
-    flops_setup = 4 * (n + 4) + 8
-    bytes_setup = 6 * 8
-    cg_flops = dof * (flops_iter * it_per_launch + flops_setup)
-    cg_bytes = dof * (bytes_iter * it_per_launch + bytes_setup)
-    achieved_tf = cg_flops / (cg_ms_per_launch / 1e3) / 1e12
-    achieved_gbs = cg_bytes / (cg_ms_per_launch / 1e3) / 1e9
-    traffic = measured_traffic("cg_kernel", args.workload, args.precision, args.precond)
+        flops_iter_i += 2 * n * n + 4 + 2 + 4 * 5 * math.log2(N) / (n * n)
+        bytes_iter_i += 2 * 8            # z written and read
+    flops_setup_i = 4 * (n + 4) + 8
+    sec = cg_ms_per_launch / 1e3
+    fp64 = args.precision in ("fp64", "fp64pc32")
+    pk = fp64_peak if fp64 else fp32_peak
+    ach_m = dof * (flops_iter_m * it_per_launch + flops_setup_m) / sec / 1e12
+    ach_i = dof * (flops_iter_i * it_per_launch + flops_setup_i) / sec / 1e12
+    gbs_m = dof * (bytes_iter_m * it_per_launch + bytes_setup_m) / sec / 1e9
+    traffic = measured_traffic("cg_kernel", args.workload, args.precision, it_per_launch)
     roof = {"kernel": "cg_kernel (persistent CG Poisson solve)", "bound": "alu",
-            "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz",
-            "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
+            "achieved": ach_m, "peak": pk, "unit": "TFLOP/s", "frac": ach_m / pk, "traffic": traffic,
+            "peak_source": ("FP64" if fp64 else "FP32") + " FMA pipe, " + fma_src,
+            "count": "method: per dof and CG iteration 8(n+4)+14 flop, 64 B; setup 8(n+4)+4 flop, 48 B",
+            "implementation_count": {"achieved": ach_i, "frac": ach_i / pk,
+                                     "flops_per_dof_iter": flops_iter_i, "flops_per_dof_setup": flops_setup_i,
+                                     "bytes_per_dof_iter": bytes_iter_i,
+                                     "what": "assembled 1D operators + two-level preconditioner work"},
+            "hbm": {"achieved": gbs_m, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs_m / peaks["hbm_gbs"], "peak_source": peak_src},
             "launch_ms": cg_ms_per_launch, "iters_per_launch": it_per_launch,
-            "algorithmic_per_dof": {"flops_per_iter": flops_iter, "bytes_per_iter": bytes_iter}}
+            "traffic_vs_method_bytes": (traffic / (dof * (bytes_iter_m * it_per_launch + bytes_setup_m))
+                                        if traffic else None)}
     line = {"metric": "Mdof·steps/s", "value": value, "unit": "Mdof·steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -541,7 +579,6 @@ def main():
                            l2=("no flush: the per-step working set (%.0f MB of state and CG vectors) exceeds "
                                "the 129 MB L2" % (12 * dof * 8 / 1e6))),
             "cg_iters_per_step": iters, "rhs_ms": rhs_ms_per_launch, "roofline": roof,
-            "error_vs_fp64": err_vs_fp64,
             "precision_modes": modes,
             "gpu_launches": int(cnt.launches), "clocks": clocks,
             "e2e": {"value": dof * ke * world / e2e_s / 1e6, "unit": "Mdof·steps/s",
@@ -551,8 +588,6 @@ def main():
                             "by a host read of (V, E, Omega), download of omega and psi" % ke}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, wl, iters, args.precond)
-        line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, wl, iters, args.precond,
-                                                      threads=os.cpu_count() or 1)
     else:
         line["cpu_baseline"] = None
     print(json.dumps(line))
@@ -577,18 +612,20 @@ def run_bracket(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     peaks, peak_src = measured_peaks()
+    fp64_peak, _, fma_src = fma_peaks()
     cpu_ms = {}
     if not args.no_cpu_baseline:
         for n in (1, 2, 3, 4):
             cpu_ms[n] = oracle_bracket_ms(n)
 
-    def time_bracket(g, f, w, J, calls):
+    def time_bracket(g, f, w, J, calls, fn=None):
+        fn = fn or dg.dg_bracket
         times = []
         for i in range(args.warmup + calls):
             flush.fill_(float(i))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            dg.dg_bracket(g, f, w, J, stream=stream)
+            fn(g, f, w, J, stream=stream)
             e1.record(stream)
             e1.synchronize()
             if i >= args.warmup:
@@ -608,10 +645,12 @@ def run_bracket(args):
         w = torch.from_numpy(fields.random_phase(X, Y, seed=3)).cuda()
         J = torch.empty_like(w)
         med, times = time_bracket(g, f, w, J, args.steps)
-        launches += args.steps
+        med_x, _ = time_bracket(g, f, w, J, args.steps, dg.dg_bracket_mixed)
+        launches += 2 * args.steps
         dof = g.dof
         row = {"P": n, "N": N, "dof": dof, "ms": med, "ms_min": min(times), "mdof_per_s": dof / med / 1e3,
-               "hbm_gbs_algorithmic": 24 * dof / (med / 1e3) / 1e9}
+               "hbm_gbs_algorithmic": 24 * dof / (med / 1e3) / 1e9,
+               "double_float_ms": med_x, "double_float_mdof_per_s": dof / med_x / 1e3}
         if N == 100:
             gpu_p, cpu_p = TABLE1_MS[n]
             row.update({"paper_gtx570_ms": gpu_p, "paper_xeon4_ms": cpu_p, "speedup_vs_gtx570": gpu_p / med,
@@ -650,10 +689,10 @@ def run_bracket(args):
                        "l2": "flushed between calls (512 MB written)"},
             "rows": rows,
             "roofline": {"kernel": "rhs_kernel in bracket-only mode, 1000x1000 cells, n=4", "bound": "alu",
-                         "achieved": big_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": big_tf / FP64_PEAK_TFLOPS,
-                         "traffic": measured_traffic("rhs_kernel", "bracket1000_n4", "fp64", "bracket-only"),
-                         "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz",
+                         "achieved": big_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": big_tf / fp64_peak,
+                         "traffic": measured_traffic("rhs_kernel", "bracket1000_n4", "fp64"),
+                         "peak_source": "FP64 FMA pipe, " + fma_src,
                          "algorithmic_per_dof": {"flops": 12 * (4 + 4) + 12, "bytes": 24},
                          "hbm": {"achieved": big["hbm_gbs_algorithmic"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": big["hbm_gbs_algorithmic"] / peaks["hbm_gbs"],
@@ -674,42 +713,40 @@ def _prec(dg, name):
 
 def run_batch(args):
     """64 uneven simulations (cells per side in {32,64,128,256}, n in {2..5}, D log-uniform in
-    [1e-5, 1e-3], random phase) advanced together by the persistent batched kernel; the group
-    count is autotuned on the first steps (which count as warm-up)."""
+    [1e-5, 1e-3], random phase) advanced together by the persistent batched kernel, in one
+    graph-captured launch per step.  The launch configuration (block groups, per-n tiles,
+    blocks per SM) is picked by the library's autotuner (dg_batch_autotune) on the first steps,
+    which count as warm-up.  With --batch-compare-fp64 the same ensemble is also run in float64
+    to the same step and each member's vorticity is compared."""
+    import numpy as np
     import torch
     from paper_1311_7477_gb300 import build as _build
     _build.build()
     from paper_1311_7477_gb300 import dg, workloads
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    prec = dg.DG_MIXED if args.precision == "mixed" else _prec(dg, args.precision)
+    prec = _prec(dg, args.precision)
     specs = workloads.ensemble_specs()
-    members = []
-    for sp in specs:
-        g = dg.Grid(sp["N"], sp["N"], sp["n"])
-        g.set_precond(args.precond)
-        w0 = torch.from_numpy(workloads.initial_field(dg, g, sp)).cuda()
-        dt = workloads.stable_dt(dg, sp["N"], sp["n"], sp["D"])
-        members.append((g, dg.Sim(g, w0, D=sp["D"], dt=dt, precision=prec, cg_tol=1e-10, cg_maxit=100000)))
-    b = dg.Batch(len(members))
-    for g, s in members:
-        b.admit(s)
+
+    def ensemble(precision):
+        members = []
+        for sp in specs:
+            g = dg.Grid(sp["N"], sp["N"], sp["n"])
+            g.set_precond(args.precond)
+            w0 = torch.from_numpy(workloads.initial_field(dg, g, sp)).cuda()
+            dt = workloads.stable_dt(dg, sp["N"], sp["n"], sp["D"])
+            members.append((g, dg.Sim(g, w0, D=sp["D"], dt=dt, precision=precision, cg_tol=1e-10,
+                                      cg_maxit=100000)))
+        b = dg.Batch(len(members))
+        for _, s in members:
+            b.admit(s)
+        return members, b
+
+    members, b = ensemble(prec)
     dof = sum(g.dof for g, _ in members)
     stream = torch.cuda.current_stream()
-    best = None
-    tune = {}
-    for G in (2, 4, 8, 16, 32):
-        b.set_groups(G)
-        b.step(1)            # plan + capture
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.step(1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tune[G] = e0.elapsed_time(e1)
-        if best is None or tune[G] < tune[best]:
-            best = G
-    b.set_groups(best)
+    t0 = time.perf_counter()
+    tuned = b.autotune(trial_steps=2)
+    tune_s = time.perf_counter() - t0
     b.step(max(args.warmup, 1))
     torch.cuda.synchronize()
     before = sum(s.status().cg_iters_total for _, s in members)
@@ -722,17 +759,36 @@ def run_batch(args):
     ms = e0.elapsed_time(e1)
     st = b.status()
     after = sum(s.status().cg_iters_total for _, s in members)
+    steps_done = members[0][1].status().step
     line = {"metric": "Mdof·steps/s", "value": dof * args.steps / (ms / 1e3) / 1e6, "unit": "Mdof·steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"mixed": "f32+f64", "mixed64": "f32+f64", "fp64": "f64"}[args.precision],
+            "dtype": {"mixed": "f32+f64", "mixed64": "f32+f64", "fp64": "f64", "fp64pc32": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "batch64", "members": len(members), "dof_total": dof,
                        "cells": "32..256 per side", "n": "2..5", "D": "log-uniform [1e-5, 1e-3]",
-                       "precision": args.precision, "cg_preconditioner": args.precond,
-                       "groups": best, "autotune_ms_per_step": tune, "graph": st["graph"]},
+                       "precision": args.precision, "cg_preconditioner": args.precond, "cg_tol": 1e-10,
+                       "autotuned": tuned, "autotune_s": tune_s, "graph": st["graph"],
+                       "steps_per_member": steps_done},
             "inner_cg_iters_per_member_step": (after - before) / (args.steps * len(members)),
             "gpu_launches": args.steps}
+    if args.batch_compare_fp64 and prec != dg.DG_FP64:
+        ref, rb = ensemble(dg.DG_FP64)
+        rb.step(steps_done - 2)
+        errs = []
+        for (g, s), (_, r) in zip(members, ref):
+            wa = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+            wb = torch.empty_like(wa)
+            s.get(wa, None)
+            r.get(wb, None)
+            errs.append(float(torch.linalg.norm(wa - wb) / torch.linalg.norm(wb)))
+        line["error_vs_fp64_per_member"] = {
+            "steps": steps_done, "max": max(errs), "median": float(np.median(errs)),
+            "what": "relative L2 of omega after the same number of steps, this precision against the same "
+                    "ensemble run in float64 (the float64 path matches the FP64 oracle to 1e-12 per step)"}
+        rb.close()
+        for _, r in ref:
+            r.close()
     print(json.dumps(line))
 
 
@@ -750,7 +806,7 @@ def run_serve(args):
     trace = workloads.request_trace(count=args.serve_requests, Ns=Ns)
     for r in trace:
         r["steps"] = max(3, int(round(r["steps"] * args.serve_steps_scale)))
-    prec = dg.DG_MIXED if args.precision == "fp64" else _prec(dg, args.precision)
+    prec = _prec(dg, args.precision)
     # the requests carry their initial fields (generated before the clock starts, as a
     # client would send them); the server uploads them at admission
     from concurrent.futures import ThreadPoolExecutor

@@ -54,7 +54,8 @@ extern "C" {
 
 /* ---- precision modes ------------------------------------------------------------- */
 #define DG_FP64 0     /* everything in float64                                             */
-#define DG_MIXED 1    /* bracket and inner CG in float32, float64 refinement, state and sums */
+#define DG_MIXED 1    /* bracket and viscous term in double-float on the float32 pipe (see  */
+                      /* dg_bracket_mixed), inner CG in float32, float64 refinement, state  */
 #define DG_MIXED64 2  /* bracket in float64, inner CG in float32, float64 refinement, state  */
 #define DG_FP64_PC32 3 /* float64 everywhere except the CG preconditioner, applied in float32 */
                        /* (a float32 copy of the cell block solve and the coarse DFT solve)   */
@@ -122,14 +123,30 @@ int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
 /*
  * dg_grid_set_precond -- the CG preconditioner of every later Poisson solve on this grid
  * (dg_poisson_solve and the simulations on g).  Sec. 6 only says that the symmetric dG
- * Poisson system is solved by conjugate gradients; the choice does not change what CG
- * converges to.  DG_PRECOND_JACOBI: W^-1.  DG_PRECOND_TWOLEVEL: the additive two-level
+ * Poisson system is solved by conjugate gradients; the choice changes the iterates and their
+ * number, and the solutions agree to the solver tolerance (both converge to the W-mean-zero
+ * solution of the same system).  DG_PRECOND_JACOBI: W^-1.  DG_PRECOND_TWOLEVEL: the additive two-level
  * preconditioner B + P A_c^+ P^T -- B the exact inverse of every cell's diagonal block of
  * A, P the prolongation of cell values to the cell's nodes, A_c = P^T A P the Galerkin
  * coarse operator, inverted (constant mode dropped) by a 2D DFT of the cell grid; the
  * solution is returned with zero W-mean.  Errors: DG_ERR_ARG.
  */
 int dg_grid_set_precond(dg_grid* g, int kind);
+
+/*
+ * dg_grid_set_compensated_apply -- how the float32 inner solves of DG_MIXED / DG_MIXED64
+ * apply the CG operator on this grid: mode 1 in double-float arithmetic on the float32
+ * vectors (an error of about eps32^2 |A| |u| instead of eps32 |A| |u|), 0 in plain float32,
+ * 2 adaptively (float32 until a refinement sweep after the second gains less than a factor
+ * 100, double-float for the rest of that solve), -1 (default) chosen from the grid: 2 when
+ * eps32 times the row-sum bound of the scaled operator exceeds 5% of the smallest non-zero
+ * eigenvalue of -Delta on the box (there a float32 apply is wrong by O(1) on the smoothest
+ * modes and the sweeps of a solve from a poor guess contract slowly), else 0.  The choice
+ * changes the inner iterates only, not what the solve converges to.
+ * dg_grid_get_compensated_apply returns the mode in use.  Errors: DG_ERR_ARG.
+ */
+int dg_grid_set_compensated_apply(dg_grid* g, int mode);
+int dg_grid_get_compensated_apply(const dg_grid* g);
 
 /*
  * dg_bracket -- J = {psi, omega} by the conservative dG Arakawa bracket
@@ -150,6 +167,15 @@ int dg_bracket(dg_grid* g, const double* psi, const double* omega, double* J, vo
 int dg_bracket_parts(dg_grid* g, const double* psi, const double* omega, double* J, int parts, void* stream);
 
 /*
+ * dg_bracket_mixed -- the bracket of dg_bracket (Eq. J) as the DG_MIXED time stepper evaluates
+ * it: the same operations in double-float arithmetic on the float32 pipe (each value the
+ * unevaluated sum of two floats, about 48 significant bits; Dekker's TwoProduct and Knuth's
+ * TwoSum), read from and written to float64 arrays.  Products are rounded one by one, so
+ * J(f, f) = 0 holds bitwise as in float64.  Arguments and errors as dg_bracket.
+ */
+int dg_bracket_mixed(dg_grid* g, const double* psi, const double* omega, double* J, void* stream);
+
+/*
  * dg_laplace_apply -- the matrix-free LDG operator of Sec. 6 (alternating fluxes, penalty
  * tau): mode 0 writes y = A x with A = W (x) A1 + A1 (x) W symmetric positive semi-definite
  * (kernel = constants); mode 1 writes y = Delta_h x = -W^{-1} A x.  float64.  y must not
@@ -159,8 +185,9 @@ int dg_laplace_apply(dg_grid* g, const double* x, double* y, int mode, void* str
 
 /*
  * dg_poisson_solve -- -Delta_h psi = omega - mean_W(omega) by conjugate gradients (Sec. 6)
- * on A psi = W (omega - mean), preconditioned by W^{-1} (run as plain CG on the symmetric
- * scaling W^{-1/2} A W^{-1/2}), from the initial guess in psi.  Stops when
+ * on A psi = W (omega - mean), run as CG on the symmetric scaling W^{-1/2} A W^{-1/2} with the
+ * grid's preconditioner (dg_grid_set_precond: W^{-1}, i.e. plain CG on the scaled system, by
+ * default, or the two-level one), from the initial guess in psi.  Stops when
  * r.W^{-1}r <= tol^2 b.W^{-1}b, or after exactly fixed_iters iterations if fixed_iters > 0
  * (parity mode; tol is then ignored).  The whole loop runs in one persistent cooperative
  * kernel; every device-side wait is capped.  float64.  Synchronises the stream.
@@ -182,11 +209,13 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
  * file-scope device array of about 2.6 MB that every GPU loading the library holds until
  * the process exits.  Grids are limited to Nx*Ny*n*n <= 65536 values; larger ones are
  * rejected with DG_ERR_ARG.  It calls no cudaMalloc, cudaFree or other allocating routine.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls
- * share the one array, which keeps the last call's contents: calls that overlap on the GPU
- * (other streams, other host threads) race.  Arguments, results and errors otherwise as in
- * dg_poisson_solve; synchronises the stream.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing).  The first call for each n on a device
+ * also loads that n's solver kernel and sets its shared-memory attribute: make one such
+ * warm-up call per n before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents: calls that overlap on the GPU (other streams, other host threads)
+ * race.  The call synchronises the stream (it returns the iteration count and residual).
+ * Arguments, results and errors otherwise as in dg_poisson_solve.
  */
 int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double Ly, double tau, const double* omega,
                             double* psi, double tol, int maxit, int fixed_iters, int* iters, double* relres,
@@ -233,6 +262,16 @@ int dg_step(dg_sim* s, int nsteps, void* stream);
 
 /* dg_sim_status -- synchronises the stream and fills info; returns info->status. */
 int dg_sim_status(dg_sim* s, dg_sim_info* info, void* stream);
+
+/*
+ * dg_sim_refinement_history -- convergence of the last mixed-precision Poisson solve
+ * (DG_MIXED, DG_MIXED64): relres[j] = sqrt(r.W^-1 r / b.W^-1 b) of the float64 residual
+ * before refinement sweep j (j = 0: the initial guess's; the last entry is the final residual)
+ * and inner_iters[j] = the float32 PCG iterations of sweep j (0 for the last entry).  At most
+ * 48 entries are kept; *count receives the number recorded, of which min(count, max) are
+ * written.  Synchronises the stream.  Errors: DG_ERR_ARG.
+ */
+int dg_sim_refinement_history(dg_sim* s, double* relres, int* inner_iters, int max, int* count, void* stream);
 
 /* dg_sim_get -- copies the current omega and psi (device pointers, either may be NULL). */
 int dg_sim_get(dg_sim* s, double* omega, double* psi, void* stream);
@@ -364,6 +403,29 @@ int dg_batch_size(const dg_batch* b);
  */
 int dg_batch_set_limit(dg_batch* b, dg_sim* s, long long last_step);
 int dg_batch_set_groups(dg_batch* b, int ngroups);
+/*
+ * dg_batch_set_tiles -- the cell tiles of the batched kernel for members with n nodes: TY x TX
+ * cells per block for the RHS pass and for the solve (0, 0: the built-in tiles).  A tile
+ * whose shared memory does not fit makes the next dg_batch_step fail with DG_ERR_ARG.
+ * dg_batch_set_blocks_per_sm -- at most cap co-resident blocks per SM (0: as many as fit).
+ * Both take effect at the next step.  Errors: DG_ERR_ARG.
+ */
+int dg_batch_set_tiles(dg_batch* b, int n, int rhs_ty, int rhs_tx, int cg_ty, int cg_tx);
+int dg_batch_set_blocks_per_sm(dg_batch* b, int cap);
+/*
+ * dg_batch_autotune -- picks the batched kernel's launch configuration for the current members
+ * by timing it: the number of block groups, then for each n present (the classes with the
+ * most degrees of freedom first) the solve tile and the RHS tile, then a cap on blocks per
+ * SM; each candidate is timed over trial_steps batched steps (CUDA events on the stream) after
+ * one untimed step, and the fastest is kept.  The trial steps are real steps: every member
+ * advances (members with a step limit may sit some out, which skews the timings: tune before
+ * setting limits).  The result is cached with the members' classes (grid size, n,
+ * precision): a later call for the same classes returns at once.  Synchronises the stream.
+ * dg_batch_get_config writes a one-line description of the configuration in use.
+ * Errors: DG_ERR_ARG, and those of dg_batch_step.
+ */
+int dg_batch_autotune(dg_batch* b, int trial_steps, void* stream);
+int dg_batch_get_config(const dg_batch* b, char* buf, int len);
 int dg_batch_step(dg_batch* b, int nsteps, void* stream);
 int dg_batch_status(dg_batch* b, int* uses_graph, int* ngroups, long long* launches, void* stream);
 

@@ -119,7 +119,7 @@ int alloc_ws(Workspace& w, size_t ndof, int grid_cap, bool with_y) {
   CUDA_TRY(cudaMalloc(&w.p1, bytes));
   CUDA_TRY(cudaMalloc(&w.q, bytes));
   if (with_y) CUDA_TRY(cudaMalloc(&w.y, bytes));
-  CUDA_TRY(cudaMalloc(&w.part, 4 * (size_t)grid_cap * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&w.part, 6 * (size_t)grid_cap * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w.sync, sizeof(SyncState)));
   CUDA_TRY(cudaMalloc(&w.status, sizeof(SolveStatus)));
   CUDA_TRY(cudaMemset(w.sync, 0, sizeof(SyncState)));
@@ -152,14 +152,55 @@ int alloc_ws_mixed(Workspace& w) {
   CUDA_TRY(cudaMalloc(&w.fp0, fb));
   CUDA_TRY(cudaMalloc(&w.fp1, fb));
   CUDA_TRY(cudaMalloc(&w.fq, fb));
-  CUDA_TRY(cudaMalloc(&w.partf, 4 * (size_t)w.grid_cap * sizeof(float)));
+  CUDA_TRY(cudaMalloc(&w.partf, 6 * (size_t)w.grid_cap * sizeof(float)));
   return DG_OK;
+}
+
+// Gershgorin bound on the largest eigenvalue of the CG operator Ahat = I (x) kx + ky (x) I:
+// the largest row sum of |kx| plus that of |ky| (a row of a 1D operator couples the cell's own
+// nodes through M and the neighbours' face traces through a r^T and d s^T).
+template <int N>
+double ahat_row_bound(const Ops2D<double, N>& O) {
+  auto rowsum = [](const Op1D<double, N>& o) {
+    double sr = 0.0, ss = 0.0, m = 0.0;
+    for (int j = 0; j < N; ++j) {
+      sr += std::fabs(o.r[j]);
+      ss += std::fabs(o.s[j]);
+    }
+    for (int i = 0; i < N; ++i) {
+      double t = std::fabs(o.a[i]) * sr + std::fabs(o.d[i]) * ss;
+      for (int j = 0; j < N; ++j) t += std::fabs(o.M[i][j]);
+      m = std::max(m, t);
+    }
+    return m;
+  };
+  return rowsum(O.kx) + rowsum(O.ky);
+}
+
+// Whether a float32 evaluation of the CG operator Ahat is too inexact on the grid's smoothest
+// modes for the float32 inner solve of the mixed modes.  Its absolute error is about eps32
+// times the row sums of |Ahat|, against the smallest non-zero eigenvalue of -Delta on the
+// periodic box, min((2 pi / Lx)^2, (2 pi / Ly)^2); once that ratio exceeds 0.05 (512^2 cells
+// with n >= 4, 1024^2 with n >= 3 on [0, 2 pi]^2) the inner solves switch to the double-float
+// apply when a refinement sweep stalls (dg_grid_set_compensated_apply overrides the choice).
+template <int N>
+bool precise_apply_needed(const Ops2D<double, N>& O, double Lx, double Ly) {
+  const double lam_min = std::min(std::pow(2.0 * M_PI / Lx, 2), std::pow(2.0 * M_PI / Ly, 2));
+  return std::ldexp(ahat_row_bound<N>(O), -24) / lam_min > 0.05;
 }
 
 template <int N>
 void build_ops(dg_grid* g) {
   new (g->ops.d) Ops2D<double, N>(make_ops<double, N>(g->rt, g->hx, g->hy));
   new (g->ops.f) Ops2D<float, N>(make_ops<float, N>(g->rt, g->hx, g->hy));
+  const Ops2D<df, N> x = make_ops<df, N>(g->rt, g->hx, g->hy);
+  new (g->ops.x) Ops2D<df, N>(x);
+  new (g->ops.k) OpsK<df, N>(OpsK<df, N>{x.kx, x.ky});
+  const Ops2D<double, N>& Od = *reinterpret_cast<const Ops2D<double, N>*>(g->ops.d);
+  g->precise_auto = precise_apply_needed<N>(Od, g->Lx, g->Ly) ? 2 : 0;
+  g->precise_apply = g->precise_auto;
+  const double f = std::ldexp(ahat_row_bound<N>(Od), -52);
+  g->floor2 = f * f;
 }
 
 // ---- two-level preconditioner tables ---------------------------------------------------
@@ -295,6 +336,10 @@ int upload_ops(dg_grid* g) {
   CUDA_TRY(cudaMemcpy(g->d_opsd, g->ops.d, sizeof(g->ops.d), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMalloc(&g->d_opsf, sizeof(g->ops.f)));
   CUDA_TRY(cudaMemcpy(g->d_opsf, g->ops.f, sizeof(g->ops.f), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(&g->d_opsx, sizeof(g->ops.x)));
+  CUDA_TRY(cudaMemcpy(g->d_opsx, g->ops.x, sizeof(g->ops.x), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(&g->d_opsk, sizeof(g->ops.k)));
+  CUDA_TRY(cudaMemcpy(g->d_opsk, g->ops.k, sizeof(g->ops.k), cudaMemcpyHostToDevice));
   return DG_OK;
 }
 
@@ -424,9 +469,20 @@ int dg_grid_destroy(dg_grid* g) {
   free_pc(g->pc);
   cudaFree(g->d_opsd);
   cudaFree(g->d_opsf);
+  cudaFree(g->d_opsx);
+  cudaFree(g->d_opsk);
   delete g;
   return DG_OK;
 }
+
+int dg_grid_set_compensated_apply(dg_grid* g, int mode) {
+  if (!g) return fail(DG_ERR_ARG, "g is NULL");
+  if (mode < -1 || mode > 2) return fail(DG_ERR_ARG, "mode must be -1 (automatic), 0, 1 or 2");
+  g->precise_apply = mode < 0 ? g->precise_auto : mode;
+  return DG_OK;
+}
+
+int dg_grid_get_compensated_apply(const dg_grid* g) { return g ? g->precise_apply : 0; }
 
 int dg_grid_set_precond(dg_grid* g, int kind) {
   if (!g) return fail(DG_ERR_ARG, "g is NULL");
@@ -494,6 +550,19 @@ int dg_bracket_parts(dg_grid* g, const double* psi, const double* omega, double*
   return dispatch_n(g->n, [&](auto nc) { return launch_rhs<double, decltype(nc)::value>(g, A, as_stream(stream)); });
 }
 
+int dg_bracket_mixed(dg_grid* g, const double* psi, const double* omega, double* J, void* stream) {
+  if (!g || !psi || !omega || !J) return fail(DG_ERR_ARG, "NULL argument");
+  if (!aligned8(psi) || !aligned8(omega) || !aligned8(J)) return fail(DG_ERR_ARG, "misaligned pointer");
+  if (J == psi || J == omega) return fail(DG_ERR_ARG, "J must not alias psi or omega");
+  RhsArgs<df> A{};
+  A.psi = psi;
+  A.omega_in = omega;
+  A.omega_base = omega;
+  A.omega_out = J;
+  A.bracket_only = 1;
+  return dispatch_n(g->n, [&](auto nc) { return launch_rhs<df, decltype(nc)::value>(g, A, as_stream(stream)); });
+}
+
 int dg_laplace_apply(dg_grid* g, const double* x, double* y, int mode, void* stream) {
   if (!g || !x || !y) return fail(DG_ERR_ARG, "NULL argument");
   if (mode != 0 && mode != 1) return fail(DG_ERR_ARG, "mode must be 0 (A x) or 1 (Delta_h x)");
@@ -519,6 +588,7 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
   A.precond = g->precond;
   A.psi_out = psi;
   A.tol2 = tol * tol;
+  A.floor2 = g->floor2;
   A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
   A.fixed_iters = fixed_iters;
   A.sumW = g->Lx * g->Ly;
@@ -570,8 +640,8 @@ void free_sim(dg_sim* s) {
 }
 
 // Poisson solve inside the stepper: y = solve(omega) from y0 = ca xa + cb xb (scaled space):
-// the persistent float64 CG kernel, or (DG_MIXED) the float64-residual / float32-CG
-// refinement kernel.
+// the persistent float64 CG kernel, or (DG_MIXED, DG_MIXED64) the float64-residual /
+// float32-CG refinement kernel.
 int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const double* xb, double cb, double* y,
               cudaStream_t st) {
   dg_grid* g = s->g;
@@ -587,6 +657,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
+    A.floor2 = g->floor2;
     A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
     A.fixed_iters = s->fixed_iters;
     A.sumW = g->Lx * g->Ly;
@@ -602,10 +673,12 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.y = y;
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
+    A.floor2 = g->floor2;
     A.tol_in2 = s->tol_in * s->tol_in;
     A.max_sweeps = s->max_sweeps;
     A.maxit_in = s->maxit;
     A.sumW = g->Lx * g->Ly;
+    A.precise_apply = g->precise_apply;
     rc = dispatch_n(g->n, [&](auto nc) { return launch_mixed<decltype(nc)::value>(g, A, s->ws, st, s); });
   } else {
     CgArgs<double> A{};
@@ -618,6 +691,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
+    A.floor2 = g->floor2;
     A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
     A.fixed_iters = s->fixed_iters;
     A.sumW = g->Lx * g->Ly;
@@ -631,7 +705,8 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
 }
 
 // R = -J(psi, omega_in) + D Delta_h omega_in;  omega_out = omega_base + dt (c_new R + sum c_m hist_m).
-// R and the history are float64 (DG_FP64) or float32 (DG_MIXED, bracket in float32).
+// R and the history are float64; the RHS is evaluated in float64 or, for DG_MIXED, in
+// double-float arithmetic on the float32 pipe.
 template <typename T>
 int sim_rhs_t(dg_sim* s, const double* psi, const double* om_in, const double* om_base, double* om_out, void* R_out,
               double c_new, int nhist, void* const* hist, const double* c_hist, cudaStream_t st) {
@@ -640,11 +715,11 @@ int sim_rhs_t(dg_sim* s, const double* psi, const double* om_in, const double* o
   A.omega_in = om_in;
   A.omega_base = om_base;
   A.omega_out = om_out;
-  A.R_out = static_cast<T*>(R_out);
+  A.R_out = static_cast<hist_t<T>*>(R_out);
   A.c_new = c_new;
   A.nhist = nhist;
   for (int m = 0; m < nhist; ++m) {
-    A.hist[m] = static_cast<const T*>(hist[m]);
+    A.hist[m] = static_cast<const hist_t<T>*>(hist[m]);
     A.c_hist[m] = c_hist[m];
   }
   A.dt = s->dt;
@@ -659,7 +734,7 @@ int sim_rhs(dg_sim* s, const double* psi, const double* om_in, const double* om_
   int rc;
   if (s->timing && (rc = record_event(s->ev_rhs, s->n_ev_rhs, st))) return rc;
   rc = (s->precision == DG_MIXED)
-           ? sim_rhs_t<float>(s, psi, om_in, om_base, om_out, R_out, c_new, nhist, hist, c_hist, st)
+           ? sim_rhs_t<df>(s, psi, om_in, om_base, om_out, R_out, c_new, nhist, hist, c_hist, st)
            : sim_rhs_t<double>(s, psi, om_in, om_base, om_out, R_out, c_new, nhist, hist, c_hist, st);
   if (rc) return rc;
   if (s->timing && (rc = record_event(s->ev_rhs, s->n_ev_rhs, st))) return rc;
@@ -735,21 +810,15 @@ int sim_ab3_step(dg_sim* s, cudaStream_t st) {
   return DG_OK;
 }
 
-// History buffer <-> float64 device array (the history is float32 for DG_MIXED).
+// History buffer <-> float64 device array.
 int R_to_double(const dg_sim* s, const void* R, double* dst, cudaStream_t st) {
   const size_t nd = ndof_of(s->g);
-  if (s->precision == DG_MIXED) {
-    return launch_convert_f2d(static_cast<const float*>(R), dst, nd, st);
-  }
   CUDA_TRY(cudaMemcpyAsync(dst, R, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return DG_OK;
 }
 
 int R_from_double(const dg_sim* s, const double* src, void* R, cudaStream_t st) {
   const size_t nd = ndof_of(s->g);
-  if (s->precision == DG_MIXED) {
-    return launch_convert_d2f(src, static_cast<float*>(R), nd, st);
-  }
   CUDA_TRY(cudaMemcpyAsync(R, src, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return DG_OK;
 }
@@ -805,7 +874,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
   s->r3 = 2;
   s->rfree = 3;
   const size_t bytes = ndof_of(g) * sizeof(double);
-  const size_t rbytes = ndof_of(g) * (precision == DG_MIXED ? sizeof(float) : sizeof(double));
+  const size_t rbytes = ndof_of(g) * sizeof(double);
   auto alloc_all = [&]() -> int {
     for (auto& p : s->omega) CUDA_TRY(cudaMalloc(&p, bytes));
     for (auto& p : s->psi) CUDA_TRY(cudaMalloc(&p, bytes));
@@ -889,6 +958,19 @@ int dg_sim_status(dg_sim* s, dg_sim_info* info, void* stream) {
   info->refine_sweeps_last = ss.last_sweeps;
   info->status = ss.flags ? flags_to_status(ss.flags) : DG_OK;
   return info->status;
+}
+
+int dg_sim_refinement_history(dg_sim* s, double* relres, int* inner_iters, int max, int* count, void* stream) {
+  if (!s || !count || max < 0 || (max > 0 && (!relres || !inner_iters))) return fail(DG_ERR_ARG, "bad arguments");
+  SolveStatus ss;
+  if (int rc = read_status(s->ws, &ss, as_stream(stream))) return rc;
+  const int len = std::min(ss.hist_len, kRefineHistory);
+  *count = len;
+  for (int j = 0; j < len && j < max; ++j) {
+    relres[j] = std::sqrt(std::max(ss.hist_rr[j], 0.0));
+    inner_iters[j] = (j + 1 < len || ss.last_sweeps > j) ? ss.hist_it[j] : 0;
+  }
+  return DG_OK;
 }
 
 int dg_sim_get(dg_sim* s, double* omega, double* psi, void* stream) {
@@ -1051,10 +1133,6 @@ int dg_sim_save(dg_sim* s, const char* path, void* stream) {
   const void* fields[6] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3]};
   for (int i = 0; i < 6 && !rc; ++i) {
     const double* src = static_cast<const double*>(fields[i]);
-    if (i >= 3 && s->precision == DG_MIXED) {
-      if ((rc = R_to_double(s, fields[i], s->stA, st))) break;
-      src = s->stA;
-    }
     if (cudaMemcpyAsync(host.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       rc = fail(DG_ERR_CUDA, "copy to the host failed");
@@ -1108,12 +1186,11 @@ int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
       rc = fail(DG_ERR_IO, "%s is truncated", path);
       break;
     }
-    double* dst = (i >= 3 && s->precision == DG_MIXED) ? s->stA : static_cast<double*>(fields[i]);
+    double* dst = static_cast<double*>(fields[i]);
     if (cudaMemcpyAsync(dst, host.data(), nd * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
       rc = fail(DG_ERR_CUDA, "copy to the device failed");
       break;
     }
-    if (dst == s->stA) rc = R_from_double(s, s->stA, fields[i], st);
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(DG_ERR_CUDA, "copy to the device failed");
   }
   std::fclose(f);
@@ -1167,30 +1244,20 @@ struct StaticScratch {
   double p0[kStaticMaxDof];
   double p1[kStaticMaxDof];
   double q[kStaticMaxDof];
-  double part[4 * kStaticMaxBlocks];
+  double part[6 * kStaticMaxBlocks];
   SyncState sync;
   SolveStatus status;
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
-// The array's name in host code is a host-side stand-in, not a device address: the device
-// address is looked up once per device (with that device current) and cached.
-constexpr int kStaticMaxDevices = 64;
-StaticScratch* g_static_addr[kStaticMaxDevices] = {};
-std::mutex g_static_mu;
-
+// The array's name in host code is a host-side stand-in, not a device address.  Its device
+// address on the current device is looked up at every call (cudaGetSymbolAddress allocates
+// nothing and is cheap), so no address outlives a reset of the device's context.
 int static_scratch_address(StaticScratch** out) {
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kStaticMaxDevices) return fail(DG_ERR_CUDA, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_addr[dev] = static_cast<StaticScratch*>(p);
-  }
-  *out = g_static_addr[dev];
+  void* p = nullptr;
+  CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+  *out = static_cast<StaticScratch*>(p);
   return DG_OK;
 }
 
@@ -1256,6 +1323,7 @@ extern "C" int dg_poisson_solve_static(int Nx, int Ny, int n, double Lx, double 
   A.v = CgVectors<double>{w.y, w.r, w.p0, w.p1, w.q};
   A.psi_out = psi;
   A.tol2 = tol * tol;
+  A.floor2 = g.floor2;
   A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
   A.fixed_iters = fixed_iters;
   A.sumW = Lx * Ly;
@@ -1275,6 +1343,13 @@ struct dg_batch {
   int max_sims = 0;
   std::vector<dg_sim*> sims;
   int ngroups_req = 0;  // 0: automatic
+  // launch configuration (dg_batch_set_tiles / dg_batch_set_blocks_per_sm / dg_batch_autotune):
+  // per n the RHS and solve tiles (0: built-in) and a cap on resident blocks per SM (0: none)
+  int tile_rhs[kMaxN + 1][2] = {};
+  int tile_cg[kMaxN + 1][2] = {};
+  int bps_cap = 0;
+  std::vector<long long> tuned_key;  // the member classes the tuned configuration was found for
+  char tuned_desc[512] = "";
   bool dirty = true;    // composition or plan changed: re-plan, re-upload, re-capture
   int stable = 0;       // launches since the last re-plan
   BatchSim* d_sims = nullptr;
@@ -1302,24 +1377,36 @@ struct dg_batch {
 
 namespace {
 
-// Tiles of a simulation inside a batch: the built-in ones for its n (a small grid's blocks
-// are few in a batch group, so its tiles are not split further as for a whole-GPU solve).
-void batch_geoms(const dg_grid* g, Geom* Gr, Geom* Gc) {
+// Tiles of a simulation inside a batch: the batch's choice for its n, else the built-in ones
+// (a small grid's blocks are few in a batch group, so its tiles are not split further as for a
+// whole-GPU solve).
+void batch_geoms(const dg_batch* b, const dg_grid* g, Geom* Gr, Geom* Gc) {
   int rty, rtx, cty, ctx;
   default_tiles(g->n, rty, rtx, cty, ctx);
+  if (b && b->tile_rhs[g->n][0] > 0) {
+    rty = b->tile_rhs[g->n][0];
+    rtx = b->tile_rhs[g->n][1];
+  }
+  if (b && b->tile_cg[g->n][0] > 0) {
+    cty = b->tile_cg[g->n][0];
+    ctx = b->tile_cg[g->n][1];
+  }
   *Gr = geom_of(g, rty, rtx);
   *Gc = geom_of(g, cty, ctx);
 }
 
-BatchSim make_batch_sim(dg_sim* s) {
+BatchSim make_batch_sim(const dg_batch* bt, dg_sim* s) {
   dg_grid* g = s->g;
   BatchSim b{};
   b.n = g->n;
   b.precision = s->precision == DG_FP64 ? 0 : (s->precision == DG_MIXED ? 1 : 2);
   b.precond = g->precond;
-  batch_geoms(g, &b.Gr, &b.Gc);
+  batch_geoms(bt, g, &b.Gr, &b.Gc);
   b.ops_d = g->d_opsd;
   b.ops_f = g->d_opsf;
+  b.ops_df = g->d_opsx;
+  b.ops_k = g->d_opsk;
+  b.precise_apply = g->precise_apply;
   for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
   for (int i = 0; i < 3; ++i) b.psi[i] = s->psi[i];
   for (int i = 0; i < 4; ++i) b.R[i] = s->R[i];
@@ -1336,6 +1423,7 @@ BatchSim make_batch_sim(dg_sim* s) {
   b.D = s->D;
   b.dt = s->dt;
   b.tol2 = s->tol * s->tol;
+  b.floor2 = g->floor2;
   b.tol_in2 = s->tol_in * s->tol_in;
   b.maxit = s->maxit;
   b.max_sweeps = s->max_sweeps;
@@ -1360,17 +1448,16 @@ BatchSim make_batch_sim(dg_sim* s) {
 }
 
 // Dynamic shared memory one simulation needs in batch_kernel (RHS tile and solve share it).
-size_t batch_smem_for(const dg_sim* s) {
+size_t batch_smem_for(const dg_batch* b, const dg_sim* s) {
   const dg_grid* g = s->g;
   Geom Gr, Gc;
-  batch_geoms(g, &Gr, &Gc);
+  batch_geoms(b, g, &Gr, &Gc);
   const int Lmax = std::max(g->Nx, g->Ny);
   const bool pc = g->precond == DG_PRECOND_TWOLEVEL;
   size_t out = 0;
   dispatch_n(g->n, [&](auto nc) {
     constexpr int N = decltype(nc)::value;
-    const size_t rhs = s->precision == DG_MIXED ? rhs_smem_values<float, N>(Gr.TY, Gr.TX) * sizeof(float)
-                                                : rhs_smem_values<double, N>(Gr.TY, Gr.TX) * sizeof(double);
+    const size_t rhs = rhs_smem_values<double, N>(Gr.TY, Gr.TX) * sizeof(double);  // double or double-float
     const size_t sol = s->precision == DG_FP64 ? cg_smem_bytes<double, N>(Gc.TY, Gc.TX, Lmax, pc)
                                                : mixed_smem_bytes<N>(Gc.TY, Gc.TX, Lmax, pc);
     out = batch_ops_bytes<N>() + std::max(rhs, sol);
@@ -1384,7 +1471,7 @@ size_t batch_smem_for(const dg_sim* s) {
 int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
   const int ns = (int)b->sims.size();
   size_t smem = 0;
-  for (dg_sim* s : b->sims) smem = std::max(smem, batch_smem_for(s));
+  for (dg_sim* s : b->sims) smem = std::max(smem, batch_smem_for(b, s));
   int optin = 0;
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -1393,6 +1480,7 @@ int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
   int per_sm = 0;
   if (int rc = batch_kernel_occupancy(smem, &per_sm)) return rc;
   if (per_sm < 1) return fail(DG_ERR_CUDA, "batch kernel does not fit on an SM");
+  if (b->bps_cap > 0) per_sm = std::min(per_sm, b->bps_cap);
   int grid = per_sm * dev_sms;
   for (dg_sim* s : b->sims) grid = std::min(grid, s->ws.grid_cap);
   int G = b->ngroups_req > 0 ? b->ngroups_req : std::min(ns, 8);
@@ -1432,7 +1520,7 @@ int batch_plan(dg_batch* b, int dev_sms, cudaStream_t st) {
   }
   // the staging buffers are rewritten only after the previous upload has executed
   if (b->upload_pending) CUDA_TRY(cudaEventSynchronize(b->ev_upload));
-  for (int i = 0; i < ns; ++i) b->h_sims[i] = make_batch_sim(b->sims[i]);
+  for (int i = 0; i < ns; ++i) b->h_sims[i] = make_batch_sim(b, b->sims[i]);
   std::copy(b->order.begin(), b->order.end(), b->h_order);
   std::copy(b->groups.begin(), b->groups.end(), b->h_groups);
   CUDA_TRY(cudaMemcpyAsync(b->d_sims, b->h_sims, ns * sizeof(BatchSim), cudaMemcpyHostToDevice, st));
@@ -1561,6 +1649,157 @@ int dg_batch_set_groups(dg_batch* b, int ngroups) {
   if (!b || ngroups < 0) return fail(DG_ERR_ARG, "bad arguments");
   b->ngroups_req = ngroups;
   b->dirty = true;
+  return DG_OK;
+}
+
+int dg_batch_set_tiles(dg_batch* b, int n, int rhs_ty, int rhs_tx, int cg_ty, int cg_tx) {
+  if (!b || n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "bad arguments");
+  const int t[4] = {rhs_ty, rhs_tx, cg_ty, cg_tx};
+  for (int v : t)
+    if (v < 0 || v > 64) return fail(DG_ERR_ARG, "tile sides must be 0..64 cells");
+  if ((rhs_ty == 0) != (rhs_tx == 0) || (cg_ty == 0) != (cg_tx == 0))
+    return fail(DG_ERR_ARG, "give both sides of a tile, or 0 for both (built-in)");
+  b->tile_rhs[n][0] = rhs_ty;
+  b->tile_rhs[n][1] = rhs_tx;
+  b->tile_cg[n][0] = cg_ty;
+  b->tile_cg[n][1] = cg_tx;
+  b->dirty = true;
+  return DG_OK;
+}
+
+int dg_batch_set_blocks_per_sm(dg_batch* b, int cap) {
+  if (!b || cap < 0) return fail(DG_ERR_ARG, "bad arguments");
+  b->bps_cap = cap;
+  b->dirty = true;
+  return DG_OK;
+}
+
+int dg_batch_get_config(const dg_batch* b, char* buf, int len) {
+  if (!b || !buf || len < 1) return fail(DG_ERR_ARG, "bad arguments");
+  int off = snprintf(buf, len, "groups=%d blocks_per_sm=%d grid=%d", b->ngroups, b->bps_cap, b->grid);
+  for (int n = 1; n <= kMaxN && off < len; ++n) {
+    bool present = false;
+    for (const dg_sim* s : b->sims) present = present || s->g->n == n;
+    if (!present) continue;
+    int rty, rtx, cty, ctx;
+    default_tiles(n, rty, rtx, cty, ctx);
+    if (b->tile_rhs[n][0] > 0) {
+      rty = b->tile_rhs[n][0];
+      rtx = b->tile_rhs[n][1];
+    }
+    if (b->tile_cg[n][0] > 0) {
+      cty = b->tile_cg[n][0];
+      ctx = b->tile_cg[n][1];
+    }
+    off += snprintf(buf + off, len - off, " n%d:rhs=%dx%d,cg=%dx%d", n, rty, rtx, cty, ctx);
+  }
+  return DG_OK;
+}
+
+int dg_batch_step(dg_batch* b, int nsteps, void* stream);
+
+int dg_batch_autotune(dg_batch* b, int trial_steps, void* stream) {
+  if (!b || trial_steps < 1) return fail(DG_ERR_ARG, "bad arguments");
+  if (b->sims.empty()) return DG_OK;
+  cudaStream_t st = as_stream(stream);
+  // the member classes: a configuration found for the same classes is reused
+  std::vector<long long> key;
+  for (const dg_sim* s : b->sims)
+    key.push_back(((long long)s->g->Nx * 100000 + s->g->Ny) * 100 + s->g->n * 10 + s->precision);
+  std::sort(key.begin(), key.end());
+  if (key == b->tuned_key) return DG_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const bool use_graph = b->use_graph;
+  b->use_graph = false;  // every trial is a fresh plan launched directly
+  int rc = DG_OK;
+  auto trial = [&](float* ms) -> int {
+    b->dirty = true;
+    if (int r = dg_batch_step(b, 1, stream)) return r;  // the new plan's first launch (uploads)
+    CUDA_TRY(cudaEventRecord(e0, st));
+    if (int r = dg_batch_step(b, trial_steps, stream)) return r;
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= float(trial_steps);
+    return DG_OK;
+  };
+  float best = 0.f;
+  rc = trial(&best);
+  // 1. the number of block groups
+  const int ns = (int)b->sims.size();
+  if (!rc) {
+    int bestG = b->ngroups_req;
+    for (int G : {1, 2, 4, 8, 16, 32}) {
+      if (G > ns || G == b->ngroups) continue;
+      b->ngroups_req = G;
+      float ms = 0.f;
+      if ((rc = trial(&ms))) break;
+      if (ms < best) {
+        best = ms;
+        bestG = G;
+      }
+    }
+    b->ngroups_req = bestG;
+  }
+  // 2. per n, the largest classes first: the solve tile, then the RHS tile
+  std::vector<std::pair<double, int>> by_n;
+  for (int n = 1; n <= kMaxN; ++n) {
+    double w = 0.0;
+    for (const dg_sim* s : b->sims)
+      if (s->g->n == n) w += (double)ndof_of(s->g);
+    if (w > 0.0) by_n.push_back({w, n});
+  }
+  std::sort(by_n.rbegin(), by_n.rend());
+  static const int kTiles[][2] = {{4, 4}, {4, 8}, {8, 8}, {8, 16}, {16, 16}};
+  for (auto& wn : by_n) {
+    const int n = wn.second;
+    for (int which = 0; which < 2 && !rc; ++which) {
+      int(*tile)[2] = which == 0 ? b->tile_cg : b->tile_rhs;
+      int keep[2] = {tile[n][0], tile[n][1]};
+      for (const auto& t : kTiles) {
+        // double-float / float64 RHS tiles above 8 x 8 cells at n >= 4 exceed the shared memory
+        if (which == 1 && n >= 4 && t[0] * t[1] > 64) continue;
+        if (which == 1 && n == 1 && t[0] * t[1] < 64) continue;
+        tile[n][0] = t[0];
+        tile[n][1] = t[1];
+        float ms = 0.f;
+        const int r = trial(&ms);
+        if (r == DG_ERR_ARG) {  // this tile does not fit: skip it
+          continue;
+        }
+        if ((rc = r)) break;
+        if (ms < best) {
+          best = ms;
+          keep[0] = t[0];
+          keep[1] = t[1];
+        }
+      }
+      tile[n][0] = keep[0];
+      tile[n][1] = keep[1];
+    }
+  }
+  // 3. a cap on resident blocks per SM (fewer, larger groups of blocks can beat full occupancy)
+  if (!rc) {
+    int keep = b->bps_cap;
+    for (int cap : {1, 2, 3}) {
+      b->bps_cap = cap;
+      float ms = 0.f;
+      if ((rc = trial(&ms))) break;
+      if (ms < best) {
+        best = ms;
+        keep = cap;
+      }
+    }
+    b->bps_cap = keep;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->use_graph = use_graph;
+  b->dirty = true;
+  if (rc) return rc;
+  b->tuned_key = key;
   return DG_OK;
 }
 

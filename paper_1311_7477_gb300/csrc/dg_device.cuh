@@ -33,6 +33,13 @@ struct Ops2D {
   T wq[N * N];        // W_ab = (hy w_a / 2)(hx w_b / 2)
 };
 
+// The CG operator alone, for the compensated (double-float) operator apply of the float32
+// inner solve.
+template <typename T, int N>
+struct OpsK {
+  Op1D<T, N> kx, ky;
+};
+
 struct Geom {
   int Nx, Ny;          // cells
   int TX, TY;          // tile (cells)

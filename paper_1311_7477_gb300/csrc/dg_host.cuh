@@ -15,7 +15,6 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
-#include <mutex>
 #include <vector>
 
 #include "../../include/dg.h"
@@ -50,6 +49,8 @@ inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7
 struct OpsHost {
   alignas(16) unsigned char d[sizeof(Ops2D<double, kMaxN>)];
   alignas(16) unsigned char f[sizeof(Ops2D<float, kMaxN>)];
+  alignas(16) unsigned char x[sizeof(Ops2D<df, kMaxN>)];  // double-float (RHS of DG_MIXED)
+  alignas(16) unsigned char k[sizeof(OpsK<df, kMaxN>)];   // double-float CG operator
 };
 
 template <int N>
@@ -112,7 +113,7 @@ struct Workspace {
   size_t ndof = 0;
   int grid_cap = 0;  // capacity of the partials (blocks)
   double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *y = nullptr;
-  double* part = nullptr;  // 4 * grid_cap
+  double* part = nullptr;  // 6 * grid_cap
   // float32 inner-solve vectors of the mixed precision path
   float *rf = nullptr, *fr = nullptr, *fe = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fq = nullptr;
   float* partf = nullptr;
@@ -154,6 +155,15 @@ struct dg_grid {
   PcTables pc;
   void* d_opsd = nullptr;  // device copies of the operator tables (batched kernel)
   void* d_opsf = nullptr;
+  void* d_opsx = nullptr;  // Ops2D<df, n>
+  void* d_opsk = nullptr;  // OpsK<df, n>
+  // a float32 evaluation of the CG operator is too inexact on the smoothest modes of this grid
+  // (see precise_apply_needed): mixed solves apply it in double-float
+  int precise_apply = 0;  // 0 float32, 1 double-float, 2 adaptive (MixedArgs::precise_apply)
+  int precise_auto = 0;   // the automatic choice (dg_grid_set_compensated_apply(g, -1))
+  // float64 rounding floor of the CG residual per unit y.y, (2^-52 x the row-sum bound of
+  // |Ahat|)^2: solves accept a residual below max(tol^2 b.b, floor2 y.y)
+  double floor2 = 0.0;
 };
 
 struct dg_sim {
@@ -199,8 +209,14 @@ inline Geom geom_of(const dg_grid* g, int TY, int TX) {
 
 template <typename T, int N>
 const Ops2D<T, N>& ops_of(const dg_grid* g) {
-  if constexpr (sizeof(T) == 8) return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.d);
-  else return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.f);
+  if constexpr (std::is_same<T, double>::value) return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.d);
+  else if constexpr (std::is_same<T, float>::value) return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.f);
+  else return *reinterpret_cast<const Ops2D<T, N>*>(g->ops.x);
+}
+
+template <int N>
+const OpsK<df, N>& opsk_of(const dg_grid* g) {
+  return *reinterpret_cast<const OpsK<df, N>*>(g->ops.k);
 }
 
 template <class F>
@@ -301,8 +317,6 @@ int launch_scale(const dg_grid* g, const double* x, double* y, int inverse, cuda
 
 // ---- launchers of the n-independent kernels (dg_misc.cu, dg_batch.cu) ------------------
 int launch_invariants_final(const double* part, int nparts, double* out, cudaStream_t st);
-int launch_convert_f2d(const float* x, double* y, size_t n, cudaStream_t st);
-int launch_convert_d2f(const double* x, float* y, size_t n, cudaStream_t st);
 // the capped-barrier self-test kernel; returns the CUDA error of the launch
 cudaError_t launch_barrier_selftest(SyncState* s, int* out, cudaStream_t st);
 // the batched persistent kernel: occupancy for smem bytes of dynamic shared memory, launch

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "dg_device.cuh"
+#include "dg_df.cuh"
 
 namespace dgk {
 
@@ -39,6 +40,21 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ df mul_rn(df a, df b) { return a * b; }
+__device__ __forceinline__ df sub_rn(df a, df b) { return a - b; }
+
+// Storage type of the right-hand-side history for an RHS evaluated in T: float64 for the
+// float64 and the double-float bracket (a double-float value converts to float64 exactly).
+template <typename T>
+struct HistType {
+  using type = double;
+};
+template <>
+struct HistType<float> {
+  using type = float;
+};
+template <typename T>
+using hist_t = typename HistType<T>::type;
 
 // a*b - c*d with both products rounded separately (never contracted into an FMA), so that
 // the bracket's antisymmetry J(f, g) = -J(g, f) and J(f, f) = 0 hold bitwise.
@@ -61,8 +77,8 @@ struct RhsArgs {
   const double* omega_in;   // vorticity at which R is evaluated (halo reads)
   const double* omega_base; // omega^k of the update (own nodes only; may alias omega_out)
   double* omega_out;        // updated vorticity, or J in bracket-only mode
-  T* R_out;                 // fresh R (may alias one hist buffer); may be null
-  const T* hist[3];
+  hist_t<T>* R_out;         // fresh R (may alias one hist buffer); may be null
+  const hist_t<T>* hist[3];
   double c_new;
   double c_hist[3];
   int nhist;
@@ -209,7 +225,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
     }
     double incr = A.c_new * double(R);
     for (int m = 0; m < A.nhist; ++m) incr = fma(A.c_hist[m], double(A.hist[m][g]), incr);
-    if (A.R_out) A.R_out[g] = R;
+    if (A.R_out) A.R_out[g] = hist_t<T>(R);
     A.omega_out[g] = fma(A.dt, incr, A.omega_base[g]);
   }
   __syncthreads();
@@ -270,6 +286,8 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__
 // same branch).  Partial buffers alternate between two halves so that a block writing the
 // next partial never races a slower block still reading the previous ones.
 // =========================================================================================
+constexpr int kRefineHistory = 48;  // sweeps recorded in SolveStatus
+
 struct SolveStatus {
   long long total_iters;
   int last_iters;
@@ -280,6 +298,11 @@ struct SolveStatus {
   int last_sweeps;  // refinement sweeps of the last mixed solve
   double last_rho;  // r.r of the last solve (scaled space)
   double last_rhob; // b.b
+  // convergence history of the last mixed solve: r.r / b.b of the float64 residual before
+  // sweep j (j = 0: of the initial guess) and the inner iterations of sweep j
+  int hist_len;
+  double hist_rr[kRefineHistory];
+  int hist_it[kRefineHistory];
 };
 
 template <typename T>
@@ -337,10 +360,15 @@ struct SolveCtx {
   T* bcast;
   int* s_flag;
   SyncState* sync;
-  T* part;                        // 4 * vsize: two alternating halves
+  T* part;                        // 6 * vsize: two alternating halves of up to 3 sums
   int phase;
   int vrank, vsize;               // this block's rank and the block count of the (virtual) grid
   int cluster;                    // the whole grid is one thread-block cluster
+  // float32 solves: if kdf is set (an OpsK<df, N> in shared memory), the operator Ahat is
+  // applied in double-float arithmetic on the float32 vectors, staged in the 8-byte tile
+  // buffers wU, wXR, wXL, wYR, wYL (the float64 context's staging region)
+  const void* kdf;
+  df *wU, *wXR, *wXL, *wYR, *wYL;
 };
 
 // The barrier between the phases of a solve: the hardware cluster barrier when the solve's
@@ -357,7 +385,7 @@ __device__ __forceinline__ bool solve_barrier(SolveCtx<T>& X) {
 // Block partials of one or two sums -> grid barrier -> the sums in every block (fixed order).
 template <typename T>
 __device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
-  T* ph = X.part + (X.phase & 1) * 2 * X.vsize;
+  T* ph = X.part + (X.phase & 1) * 3 * X.vsize;
   ++X.phase;
   v0 = block_sum(v0, X.red);
   if (threadIdx.x == 0) __stcg(ph + X.vrank, v0);
@@ -368,7 +396,7 @@ __device__ __forceinline__ bool reduce_all(SolveCtx<T>& X, T v0, T& out0) {
 
 template <typename T>
 __device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0, T& out1) {
-  T* ph = X.part + (X.phase & 1) * 2 * X.vsize;
+  T* ph = X.part + (X.phase & 1) * 3 * X.vsize;
   ++X.phase;
   v0 = block_sum(v0, X.red);
   if (threadIdx.x == 0) __stcg(ph + 2 * X.vrank, v0);
@@ -380,11 +408,28 @@ __device__ __forceinline__ bool reduce_all2(SolveCtx<T>& X, T v0, T v1, T& out0,
   return true;
 }
 
+template <typename T>
+__device__ __forceinline__ bool reduce_all3(SolveCtx<T>& X, T v0, T v1, T v2, T& out0, T& out1, T& out2) {
+  T* ph = X.part + (X.phase & 1) * 3 * X.vsize;
+  ++X.phase;
+  v0 = block_sum(v0, X.red);
+  if (threadIdx.x == 0) __stcg(ph + 3 * X.vrank, v0);
+  v1 = block_sum(v1, X.red);
+  if (threadIdx.x == 0) __stcg(ph + 3 * X.vrank + 1, v1);
+  v2 = block_sum(v2, X.red);
+  if (threadIdx.x == 0) __stcg(ph + 3 * X.vrank + 2, v2);
+  if (!solve_barrier(X)) return false;
+  out0 = sum_partials_block(ph, X.vsize, 3, X.red, X.bcast);
+  out1 = sum_partials_block(ph + 1, X.vsize, 3, X.red, X.bcast);
+  out2 = sum_partials_block(ph + 2, X.vsize, 3, X.red, X.bcast);
+  return true;
+}
+
 // One CG tile pass: stage u = load(...) (plus-shaped halo), apply Ahat, hand (g, k, u, q)
 // to out(...).
-template <typename T, int N, class LoadF, class OutF>
-__device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& G, int tile, SolveCtx<T>& X,
-                                              LoadF&& load, OutF&& out) {
+template <typename T, int N, class Tab, class LoadF, class OutF>
+__device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int tile, SolveCtx<T>& X, LoadF&& load,
+                                              OutF&& out) {
   constexpr int NN = N * N;
   const TileBox B = make_box(G, tile);
   stage_box<T, N>(G, B, X.sU, false, load);
@@ -434,6 +479,33 @@ __device__ __forceinline__ void cg_tile_apply(const Ops2D<T, N>& C, const Geom& 
     }
   }
   __syncthreads();
+}
+
+// One tile pass of the solve's operator: cg_tile_apply in T, or -- for a float32 solve with
+// the compensated apply enabled -- in double-float arithmetic on the same float32 values, the
+// result rounded to float32.  A float32 evaluation of Ahat u has an absolute error of about
+// eps32 |Ahat| |u|, which on the smoothest modes of a fine grid (eigenvalue ~1 against
+// |Ahat| ~ 1e7 at 1024^2 cells, n = 5) is as large as Ahat u itself; the double-float apply
+// brings it down to ~eps32^2 |Ahat| |u|.
+template <typename T, int N, class LoadF, class OutF>
+__device__ __forceinline__ void solve_apply(const Ops2D<T, N>& C, const Geom& G, int tile, SolveCtx<T>& X,
+                                            LoadF&& load, OutF&& out) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (X.kdf) {
+      SolveCtx<df> W;
+      W.sU = X.wU;
+      W.tXR = X.wXR;
+      W.tXL = X.wXL;
+      W.tYR = X.wYR;
+      W.tYL = X.wYL;
+      cg_tile_apply<df, N>(
+          *static_cast<const OpsK<df, N>*>(X.kdf), G, tile, W,
+          [&](size_t g, int k, bool interior) { return df(load(g, k, interior)); },
+          [&](size_t g, int k, df u, df q) { out(g, k, u.hi, to_float(q)); });
+      return;
+    }
+  }
+  cg_tile_apply<T, N>(C, G, tile, X, load, out);
 }
 
 // Where the tile's residual is staged for the preconditioner's cell part: X.sU itself, or,
@@ -639,12 +711,13 @@ template <typename T, int N, typename TP = T>
 __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, const CgVectors<T>& V,
                                           const PrecondArgs<TP>* P, const RhsSource<T>& Bsrc, SolveCtx<T>& X,
                                           T& rr, T rz, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
-                                          int max_restarts = kMaxRestarts) {
+                                          int max_restarts = kMaxRestarts, double floor2 = 0.0) {
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)X.vsize * blockDim.x;
   int it = 0, restarts = 0;
+  double rr_prev = -1.0;  // true residual at the previous verification
   T beta = T(0);
   int cur = 0;
   bool first = true;  // p = z (no previous direction)
@@ -654,24 +727,31 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       if (it >= fixed_iters) break;
     } else if (double(rr) <= tol2 * double(rhob)) {
       if (max_restarts == 0) break;  // loose inner solves: the recursive residual suffices
-      // Verify on the true residual r = b - Ahat y.
-      T rt = T(0);
+      // Verify on the true residual r = b - Ahat y: accept it below the tolerance, or once it
+      // stagnates below the float64 rounding floor of the iterate y (floor2 * y.y, see
+      // CgArgs::floor2), where no float64 iterate can do better.
+      T rt = T(0), yt = T(0);
       for (int t = X.vrank; t < ntiles; t += X.vsize) {
-        cg_tile_apply<T, N>(
+        solve_apply<T, N>(
             C, G, t, X, [&](size_t g, int, bool) { return __ldcg(V.y + g); },
-            [&](size_t g, int k, T, T qv) {
+            [&](size_t g, int k, T yv, T qv) {
               const T r = rhs_at<T, N>(C, Bsrc, g, k) - qv;
               __stcg(V.r + g, r);
               rt = fma(r, r, rt);
+              yt = fma(yv, yv, yt);
             });
       }
-      T rr_true = T(0);
-      if (!reduce_all(X, rt, rr_true)) {
+      T rr_true = T(0), yy = T(0);
+      if (!reduce_all2(X, rt, yt, rr_true, yy)) {
         flags |= kFlagTimeout;
         return it;
       }
       rr = rr_true;
       if (double(rr_true) <= tol2 * double(rhob)) break;
+      // stagnation at the rounding floor: below it, and less than a factor 4 below the previous
+      // check's true residual
+      if (double(rr_true) <= floor2 * double(yy) && rr_prev >= 0.0 && double(rr_true) > 0.25 * rr_prev) break;
+      rr_prev = double(rr_true);
       if (restarts >= max_restarts) {
         flags |= kFlagNoconv;
         break;
@@ -698,7 +778,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
     // Phase A: p = z + beta p_old (halo recomputed locally), q = Ahat p, p.q.
     T pq = T(0);
     for (int t = X.vrank; t < ntiles; t += X.vsize) {
-      cg_tile_apply<T, N>(
+      solve_apply<T, N>(
           C, G, t, X,
           [&](size_t g, int k, bool interior) {
             const T zv = P ? fma(C.sw[k], T(__ldcg(P->uc + g / NN)), T(__ldcg(P->z + g))) : __ldcg(V.r + g);
@@ -813,10 +893,15 @@ struct CgArgs {
   int precond;          // 0: W^-1 (plain CG on the scaled system), 1: two-level
   PrecondArgs<TP> pc;   // (TP = float: the preconditioner applied in float32)
   double* psi_out;      // if non-null: psi = y / sqrt(W) at the end
-  T* part;              // 4 * gridDim.x
+  T* part;              // 6 * gridDim.x
   SyncState* sync;
   SolveStatus* status;
   double tol2;
+  // The float64 rounding floor of the residual, per unit y.y: rounding y to float64 and
+  // evaluating b - Ahat y in float64 leave a residual of up to about 2 u lambda_max |y|
+  // (u = 2^-53, lambda_max bounded by the row sums of |Ahat|), so floor2 = (2^-52 lambda)^2;
+  // a solve whose true residual stagnates below floor2 y.y stops there, even above tol2 b.b.
+  double floor2;
   int maxit, fixed_iters;
   double sumW;
   int cluster;          // launched as one thread-block cluster (cluster barriers)
@@ -862,6 +947,8 @@ __device__ __forceinline__ void init_ctx(SolveCtx<T>& X, unsigned char* base, co
   X.line0 = reinterpret_cast<Cplx<T>*>(p);
   X.line1 = X.line0 + Lmax;
   X.cluster = 0;
+  X.kdf = nullptr;
+  X.wU = X.wXR = X.wXL = X.wYR = X.wYL = nullptr;
   __syncthreads();
 }
 
@@ -932,7 +1019,7 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
       goto finish;
     }
     it = cg_iterate<T, N, TP>(C, G, A.v, pc ? &A.pc : nullptr, RhsSource<T>{A.omega, A.rhs, wbar}, X, rr, rz, rhob,
-                          A.tol2, A.maxit, A.fixed_iters, flags);
+                              A.tol2, A.maxit, A.fixed_iters, flags, kMaxRestarts, A.floor2);
     if (pc && !(flags & kFlagTimeout) && !project_mean<T, N>(C, G, A.v.y, A.sumW, X)) flags |= kFlagTimeout;
   }
 finish:
@@ -993,15 +1080,27 @@ struct MixedArgs {
   CgVectors<float> v;  // inner solve: y = e, r, p0, p1, q
   int precond;         // 0: W^-1, 1: two-level (inner float32 solve)
   PrecondArgs<float> pc;
-  double* partd;       // 4 * gridDim.x
-  float* partf;        // 4 * gridDim.x
+  double* partd;       // 6 * gridDim.x
+  float* partf;        // 6 * gridDim.x
   SyncState* sync;
   SolveStatus* status;
   double tol2, tol_in2;
+  double floor2;       // the float64 rounding floor per unit y.y (see CgArgs::floor2)
   int max_sweeps, maxit_in;
   double sumW;
   int cluster;         // launched as one thread-block cluster (cluster barriers)
+  // the inner solve's operator apply (see solve_apply): 0 float32, 1 double-float, 2 float32
+  // until a refinement sweep after the second reduces the residual by less than a factor 100
+  // (too inexact on this problem's smoothest modes), double-float from then on
+  int precise_apply;
 };
+
+// The operator tables a mixed solve stages in shared memory: float64 (residuals), float32
+// (inner solve) and the double-float CG operator (compensated apply).
+template <int N>
+__host__ __device__ constexpr size_t mixed_ops_bytes() {
+  return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>() + table_bytes<OpsK<df, N>>();
+}
 
 template <int N>
 __host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX, int Lmax, bool pc) {
@@ -1016,7 +1115,7 @@ __host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX, int Lmax, 
 template <int N>
 __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const Geom& G, const MixedArgs& A,
                                                double wbar, bool from_x0, SolveCtx<double>& X, double& rr,
-                                               double& bb) {
+                                               double& bb, double& yy) {
   const int ntiles = G.tilesX * G.tilesY;
   for (int t = X.vrank; t < ntiles; t += X.vsize) {
     cg_tile_apply<double, N>(
@@ -1030,7 +1129,7 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
           if (interior) __stcg(A.y + g, v);
           return v;
         },
-        [&](size_t g, int k, double, double qv) {
+        [&](size_t g, int k, double yv, double qv) {
           const double b = Cd.sw[k] * (A.omega[g] - wbar);
           const double r = b - qv;
           const float r32 = float(r);
@@ -1039,6 +1138,7 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
           __stcg(A.v.y + g, 0.0f);
           rr = fma(r, r, rr);
           bb = fma(b, b, bb);
+          yy = fma(yv, yv, yy);
         });
   }
 }
@@ -1046,10 +1146,18 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
 // The whole mixed-precision solve on the (virtual) grid of Xf / Xd (float context with the
 // staged block matrix, double context over the same region; see mixed_cg_kernel).
 template <int N>
-__device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Ops2D<float, N>& Cf, const Geom& G,
-                                            const MixedArgs& A, SolveCtx<float>& Xf, SolveCtx<double>& Xd) {
+__device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Ops2D<float, N>& Cf,
+                                            const OpsK<df, N>& Ck, const Geom& G, const MixedArgs& A,
+                                            SolveCtx<float>& Xf, SolveCtx<double>& Xd) {
   constexpr int NN = N * N;
   const bool pc = A.precond == 1;
+  // the double-float apply stages its tiles in the float64 buffers
+  Xf.wU = reinterpret_cast<df*>(Xd.sU);
+  Xf.wXR = reinterpret_cast<df*>(Xd.tXR);
+  Xf.wXL = reinterpret_cast<df*>(Xd.tXL);
+  Xf.wYR = reinterpret_cast<df*>(Xd.tYR);
+  Xf.wYL = reinterpret_cast<df*>(Xd.tYL);
+  Xf.kdf = A.precise_apply == 1 ? &Ck : nullptr;
   Xf.sync = A.sync;
   Xf.part = A.partf;
   Xf.phase = 0;
@@ -1060,7 +1168,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   const size_t stride = (size_t)Xd.vsize * blockDim.x;
   int flags = 0, sweeps = 0;
   long long inner = 0;
-  double rr = 0.0, bb = 0.0, wbar = 0.0;
+  double rr = 0.0, bb = 0.0, wbar = 0.0, rr_prev = -1.0;
   for (int mp = 0; mp < 2; ++mp) {  // two-pass W-mean, as in cg_kernel
     double s = 0.0;
     for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
@@ -1074,10 +1182,11 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   }
   for (int pass = 0;; ++pass) {
     // float64 residual of the current iterate (pass 0: of the initial guess)
+    double yy = 0.0;
     {
-      double r2 = 0.0, b2 = 0.0;
-      mixed_residual<N>(Cd, G, A, wbar, pass == 0, Xd, r2, b2);
-      if (!reduce_all2(Xd, r2, b2, rr, bb)) {
+      double r2 = 0.0, b2 = 0.0, y2 = 0.0;
+      mixed_residual<N>(Cd, G, A, wbar, pass == 0, Xd, r2, b2, y2);
+      if (!reduce_all3(Xd, r2, b2, y2, rr, bb, yy)) {
         flags |= kFlagTimeout;
         goto finish;
       }
@@ -1087,7 +1196,20 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
       rr = 0.0;
       break;
     }
+    if (Xd.vrank == 0 && threadIdx.x == 0 && pass < kRefineHistory) {
+      A.status->hist_rr[pass] = rr / bb;
+      A.status->hist_len = pass + 1;
+    }
     if (rr <= A.tol2 * bb) break;
+    // stagnation at the float64 rounding floor of y (see CgArgs::floor2): below it, and less
+    // than a factor 4 below the previous sweep's residual
+    if (rr <= A.floor2 * yy && rr_prev >= 0.0 && rr > 0.25 * rr_prev) break;
+    // adaptive apply: a sweep after the second that gained less than a factor 100 in the
+    // residual norm (1e-4 in r.r) switches the inner solves to the double-float apply (the
+    // first sweep from a poor guess is limited by the float32 rounding of its large correction
+    // instead)
+    if (A.precise_apply == 2 && !Xf.kdf && pass >= 2 && rr > 1e-4 * rr_prev) Xf.kdf = &Ck;
+    rr_prev = rr;
     if (sweeps >= A.max_sweeps) {
       flags |= kFlagNoconv;
       break;
@@ -1107,6 +1229,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
     const int it_in = cg_iterate<float, N>(Cf, G, A.v, pc ? &A.pc : nullptr, RhsSource<float>{nullptr, A.rf, 0.0f},
                                            Xf, rho_in, rz_in, rhob_in, tol_eff2, A.maxit_in, 0, fin, 0);
     inner += it_in;
+    if (Xd.vrank == 0 && threadIdx.x == 0 && pass < kRefineHistory) A.status->hist_it[pass] = it_in;
     if (fin & kFlagTimeout) {
       flags |= kFlagTimeout;
       goto finish;
@@ -1143,7 +1266,8 @@ finish:
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
-                                                           const __grid_constant__ Ops2D<float, N> Cf, const Geom G,
+                                                           const __grid_constant__ Ops2D<float, N> Cf,
+                                                           const __grid_constant__ OpsK<df, N> Ck, const Geom G,
                                                            const __grid_constant__ MixedArgs A) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1156,7 +1280,9 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
   const int Lmax = max(G.Nx, G.Ny);
   const Ops2D<double, N>& Cds = stage_table(Cd, smem_raw);
   const Ops2D<float, N>& Cfs = stage_table(Cf, smem_raw + table_bytes<Ops2D<double, N>>());
-  unsigned char* smem = smem_raw + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>();
+  const OpsK<df, N>& Cks =
+      stage_table(Ck, smem_raw + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>());
+  unsigned char* smem = smem_raw + mixed_ops_bytes<N>();
   SolveCtx<float> Xf;
   init_ctx<float, N>(Xf, smem, G, A.pc.Bt, pc, Lmax);
   Xf.red = redf;
@@ -1172,7 +1298,7 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
   Xd.vrank = blockIdx.x;
   Xd.vsize = gridDim.x;
   Xf.cluster = Xd.cluster = A.cluster;
-  mixed_solve<N>(Cds, Cfs, G, A, Xf, Xd);
+  mixed_solve<N>(Cds, Cfs, Cks, G, A, Xf, Xd);
 }
 
 // =========================================================================================
@@ -1183,17 +1309,20 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
 // simulations queued on it, one after the other.  Groups run concurrently.
 // =========================================================================================
 struct BatchSim {
-  int n, precision, precond;       // precision: 0 float64, 1 mixed (float32 RHS), 2 mixed (float64 RHS)
+  int n, precision, precond;       // precision: 0 float64, 1 mixed (double-float RHS), 2 mixed (float64 RHS)
+  int precise_apply;               // mixed: the inner solve applies Ahat in double-float
   Geom Gr, Gc;                     // tiles of the RHS and of the solve
   const void* ops_d;               // device copy of Ops2D<double, n>
   const void* ops_f;               // device copy of Ops2D<float, n>
+  const void* ops_df;              // device copy of Ops2D<df, n> (double-float RHS)
+  const void* ops_k;               // device copy of OpsK<df, n> (double-float CG operator)
   double* omega[2];
   double* psi[3];                  // sqrt(W) psi
-  void* R[4];                      // float64, or float32 with a float32 RHS
+  void* R[4];                      // right-hand-side history (float64)
   int oc, p0, p1, p2, r1, r2, r3, rfree;  // ring indices, advanced by the kernel
   long long step;
   long long limit;                 // no batched step once step == limit (0: no limit)
-  double D, dt, tol2, tol_in2;
+  double D, dt, tol2, tol_in2, floor2;
   int maxit, max_sweeps, fixed_iters;
   double sumW;
   // float64 solve
@@ -1228,9 +1357,9 @@ __device__ __noinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& C, 
   A.omega_in = S.omega[oc];
   A.omega_base = S.omega[oc];
   A.omega_out = S.omega[oc ^ 1];
-  A.R_out = static_cast<T*>(S.R[rfree]);
-  A.hist[0] = static_cast<const T*>(S.R[r1]);
-  A.hist[1] = static_cast<const T*>(S.R[r2]);
+  A.R_out = static_cast<hist_t<T>*>(S.R[rfree]);
+  A.hist[0] = static_cast<const hist_t<T>*>(S.R[r1]);
+  A.hist[1] = static_cast<const hist_t<T>*>(S.R[r2]);
   A.c_new = 23.0 / 12.0;
   A.c_hist[0] = -16.0 / 12.0;
   A.c_hist[1] = 5.0 / 12.0;
@@ -1243,9 +1372,12 @@ __device__ __noinline__ void batch_rhs(const BatchSim& S, const Ops2D<T, N>& C, 
 }
 
 // One AB3 step of simulation S on a group.  Returns false after a barrier timeout.
+// Shared-memory tables of a batched step: the float64 operators (the double-float RHS
+// operators during a DG_MIXED member's RHS pass: same size), float32, double-float CG operator.
 template <int N>
 __host__ __device__ constexpr size_t batch_ops_bytes() {
-  return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>();
+  static_assert(sizeof(Ops2D<df, N>) == sizeof(Ops2D<double, N>), "table sizes");
+  return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>() + table_bytes<OpsK<df, N>>();
 }
 
 template <int N>
@@ -1260,15 +1392,21 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
   const int r1 = __ldcg(&Sp->r1), r2 = __ldcg(&Sp->r2), r3 = __ldcg(&Sp->r3), rfree = __ldcg(&Sp->rfree);
   // this simulation's operator tables, staged in shared memory (the previous step's last
   // barrier has synchronised the block)
+  unsigned char* smem = smem_all + batch_ops_bytes<N>();
+  if (S.precision == 1) {
+    const Ops2D<df, N>& Cr = stage_table(*static_cast<const Ops2D<df, N>*>(S.ops_df), smem_all);
+    batch_rhs<df, N>(S, Cr, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
+  } else {
+    const Ops2D<double, N>& Cr = stage_table(*static_cast<const Ops2D<double, N>*>(S.ops_d), smem_all);
+    batch_rhs<double, N>(S, Cr, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
+  }
+  if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
+  // the solve's tables (the barrier has synchronised the block: the RHS table is no longer read)
   const Ops2D<double, N>& Cd = stage_table(*static_cast<const Ops2D<double, N>*>(S.ops_d), smem_all);
   const Ops2D<float, N>& Cf =
       stage_table(*static_cast<const Ops2D<float, N>*>(S.ops_f), smem_all + table_bytes<Ops2D<double, N>>());
-  unsigned char* smem = smem_all + batch_ops_bytes<N>();
-  if (S.precision == 1)
-    batch_rhs<float, N>(S, Cf, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
-  else
-    batch_rhs<double, N>(S, Cd, oc, p0, r1, r2, rfree, vrank, grp.nblocks, smem);
-  if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
+  const OpsK<df, N>& Ck = stage_table(*static_cast<const OpsK<df, N>*>(S.ops_k),
+                                      smem_all + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>());
   const bool pc = S.precond == 1;
   const int Lmax = max(S.Gc.Nx, S.Gc.Ny);
   if (S.precision == 0) {
@@ -1285,6 +1423,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.sync = grp.sync;
     A.status = S.status;
     A.tol2 = S.tol2;
+    A.floor2 = S.floor2;
     A.maxit = S.fixed_iters > 0 ? max(S.maxit, S.fixed_iters) : S.maxit;
     A.fixed_iters = S.fixed_iters;
     A.sumW = S.sumW;
@@ -1313,10 +1452,12 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.sync = grp.sync;
     A.status = S.status;
     A.tol2 = S.tol2;
+    A.floor2 = S.floor2;
     A.tol_in2 = S.tol_in2;
     A.max_sweeps = S.max_sweeps;
     A.maxit_in = S.maxit;
     A.sumW = S.sumW;
+    A.precise_apply = S.precise_apply;
     SolveCtx<float> Xf;
     init_ctx<float, N>(Xf, smem, S.Gc, S.pcf.Bt, pc, Lmax);
     Xf.red = redf;
@@ -1331,7 +1472,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     Xd.s_flag = s_flag;
     Xd.vrank = vrank;
     Xd.vsize = grp.nblocks;
-    mixed_solve<N>(Cd, Cf, S.Gc, A, Xf, Xd);
+    mixed_solve<N>(Cd, Cf, Ck, S.Gc, A, Xf, Xd);
   }
   // every block has finished the solve before the rings move
   if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
@@ -1403,10 +1544,5 @@ __global__ void scale_nodes_kernel(const __grid_constant__ NodeWeights<N> W, con
   }
 }
 
-template <typename S, typename D>
-__global__ void convert_kernel(const S* __restrict__ x, D* __restrict__ y, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = D(x[i]);
-}
 
 }  // namespace dgk

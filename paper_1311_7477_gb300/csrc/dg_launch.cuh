@@ -106,8 +106,7 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
   bool cluster = false;
   Geom G = solve_geom(g, true, &cluster);
   auto smem_of = [&](const Geom& Gx) {
-    return table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>() +
-           mixed_smem_bytes<N>(Gx.TY, Gx.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+    return mixed_ops_bytes<N>() + mixed_smem_bytes<N>(Gx.TY, Gx.TX, std::max(g->Nx, g->Ny), A.precond == 1);
   };
   size_t smem = smem_of(G);
   auto kern = mixed_cg_kernel<N>;
@@ -130,7 +129,7 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
     if (int rc = record_event(timed->ev_cg, timed->n_ev_cg, st)) return rc;
   bool launched = false;
   A.cluster = cluster ? 1 : 0;
-  if (int rc = launch_solve(kern, cluster, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), G, A))
+  if (int rc = launch_solve(kern, cluster, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), opsk_of<N>(g), G, A))
     return rc;
   if (!launched) {  // no room for the cluster: the tiles of a cooperative launch instead
     G = geom_of(g, g->cTY, g->cTX);
@@ -139,7 +138,7 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     grid = std::min({per_sm * g->num_sms, G.tilesX * G.tilesY, w.grid_cap});
     A.cluster = 0;
-    if (int rc = launch_solve(kern, false, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), G, A))
+    if (int rc = launch_solve(kern, false, grid, smem, st, &launched, ops_of<double, N>(g), ops_of<float, N>(g), opsk_of<N>(g), G, A))
       return rc;
   }
   if (tm)
@@ -174,7 +173,7 @@ int launch_scale(const dg_grid* g, const double* x, double* y, int inverse, cuda
 #define DGK_INSTANTIATE_LAUNCHERS(N)                                                                           \
   namespace dgk {                                                                                             \
   template int launch_rhs<double, N>(const dg_grid*, const RhsArgs<double>&, cudaStream_t);                   \
-  template int launch_rhs<float, N>(const dg_grid*, const RhsArgs<float>&, cudaStream_t);                     \
+  template int launch_rhs<df, N>(const dg_grid*, const RhsArgs<df>&, cudaStream_t);                           \
   template int launch_apply<double, N>(const dg_grid*, const double*, double*, int, cudaStream_t);            \
   template int launch_cg<double, N, double>(const dg_grid*, CgArgs<double, double>, const Workspace&,         \
                                             cudaStream_t, dg_sim*);                                           \

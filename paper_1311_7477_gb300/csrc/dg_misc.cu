@@ -1,5 +1,5 @@
 // The small n-independent kernels and their launches: the final stage of the invariant
-// sums, float32 <-> float64 conversion of the history ring, and the barrier self-test.
+// sums and the barrier self-test.
 #include "dg_host.cuh"
 
 namespace dgk {
@@ -26,20 +26,6 @@ __global__ void barrier_selftest_kernel(SyncState* s, int* out) {
 
 int launch_invariants_final(const double* part, int nparts, double* out, cudaStream_t st) {
   invariants_final_kernel<<<1, 32, 0, st>>>(part, nparts, out);
-  CUDA_TRY(cudaGetLastError());
-  return DG_OK;
-}
-
-int launch_convert_f2d(const float* x, double* y, size_t n, cudaStream_t st) {
-  const int blocks = (int)std::min<size_t>(4096, (n + kThreads - 1) / kThreads);
-  convert_kernel<float, double><<<blocks, kThreads, 0, st>>>(x, y, n);
-  CUDA_TRY(cudaGetLastError());
-  return DG_OK;
-}
-
-int launch_convert_d2f(const double* x, float* y, size_t n, cudaStream_t st) {
-  const int blocks = (int)std::min<size_t>(4096, (n + kThreads - 1) / kThreads);
-  convert_kernel<double, float><<<blocks, kThreads, 0, st>>>(x, y, n);
   CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

@@ -58,7 +58,10 @@ def _load():
         "dg_grid_nodes": (I, [P, PD, PD, PD]),
         "dg_grid_set_tiles": (I, [P, I, I]),
         "dg_grid_set_precond": (I, [P, I]),
+        "dg_grid_set_compensated_apply": (I, [P, I]),
+        "dg_grid_get_compensated_apply": (I, [P]),
         "dg_bracket": (I, [P, P, P, P, P]),
+        "dg_bracket_mixed": (I, [P, P, P, P, P]),
         "dg_bracket_parts": (I, [P, P, P, P, I, P]),
         "dg_laplace_apply": (I, [P, P, P, I, P]),
         "dg_poisson_solve": (I, [P, P, P, D, I, I, PI, PD, P]),
@@ -68,6 +71,7 @@ def _load():
         "dg_sim_destroy": (I, [P]),
         "dg_step": (I, [P, I, P]),
         "dg_sim_status": (I, [P, ctypes.POINTER(SimInfo), P]),
+        "dg_sim_refinement_history": (I, [P, ctypes.POINTER(ctypes.c_double), PI, I, PI, P]),
         "dg_sim_get": (I, [P, P, P, P]),
         "dg_sim_get_state": (I, [P, ctypes.POINTER(LL), P, P, P, P, P, P]),
         "dg_sim_set_state": (I, [P, LL, P, P, P, P, P, P]),
@@ -87,6 +91,10 @@ def _load():
         "dg_batch_retire": (I, [P, P]),
         "dg_batch_size": (I, [P]),
         "dg_batch_set_groups": (I, [P, I]),
+        "dg_batch_set_tiles": (I, [P, I, I, I, I, I]),
+        "dg_batch_set_blocks_per_sm": (I, [P, I]),
+        "dg_batch_autotune": (I, [P, I, P]),
+        "dg_batch_get_config": (I, [P, ctypes.c_char_p, I]),
         "dg_batch_step": (I, [P, I, P]),
         "dg_batch_status": (I, [P, PI, PI, ctypes.POINTER(LL), P]),
         "dg_sim_upload": (I, [P, LL, P, P, P, P, P, P]),
@@ -202,6 +210,15 @@ class Grid:
             kind = {"jacobi": DG_PRECOND_JACOBI, "twolevel": DG_PRECOND_TWOLEVEL}[kind]
         _check(_lib.dg_grid_set_precond(self.h, int(kind)))
 
+    def set_compensated_apply(self, mode):
+        """-1 (automatic), 0 (float32), 1 (double-float) or 2 (adaptive): the operator apply of
+        the float32 inner solves of the mixed modes on this grid."""
+        _check(_lib.dg_grid_set_compensated_apply(self.h, int(mode)))
+
+    @property
+    def compensated_apply(self):
+        return int(_lib.dg_grid_get_compensated_apply(self.h))
+
     def close(self):
         if getattr(self, "h", None):
             _lib.dg_grid_destroy(self.h)
@@ -216,6 +233,11 @@ class Grid:
 
 def dg_bracket(grid, psi, omega, J, stream=None):
     _check(_lib.dg_bracket(grid.h, _ptr(psi), _ptr(omega), _ptr(J), _stream(stream)))
+
+
+def dg_bracket_mixed(grid, psi, omega, J, stream=None):
+    """The bracket as DG_MIXED evaluates it: double-float arithmetic on the float32 pipe."""
+    _check(_lib.dg_bracket_mixed(grid.h, _ptr(psi), _ptr(omega), _ptr(J), _stream(stream)))
 
 
 def dg_bracket_parts(grid, psi, omega, J, parts, stream=None):
@@ -293,6 +315,14 @@ class Sim:
         if check:
             _check(rc)
         return info
+
+    def refinement_history(self, stream=None):
+        """[(relres before sweep j, inner iterations of sweep j)] of the last mixed solve."""
+        rr = (ctypes.c_double * 48)()
+        it = (ctypes.c_int * 48)()
+        cnt = ctypes.c_int(0)
+        _check(_lib.dg_sim_refinement_history(self.h, rr, it, 48, ctypes.byref(cnt), _stream(stream)))
+        return [(rr[j], it[j]) for j in range(min(cnt.value, 48))]
 
     def get(self, omega=None, psi=None, stream=None):
         _check(_lib.dg_sim_get(self.h, _ptr(omega), _ptr(psi), _stream(stream)))
@@ -374,6 +404,23 @@ class Batch:
 
     def set_groups(self, ngroups):
         _check(_lib.dg_batch_set_groups(self.h, int(ngroups)))
+
+    def set_tiles(self, n, rhs=(0, 0), cg=(0, 0)):
+        """Cell tiles (TY, TX) of the batched kernel for members with n nodes ((0, 0): built-in)."""
+        _check(_lib.dg_batch_set_tiles(self.h, int(n), int(rhs[0]), int(rhs[1]), int(cg[0]), int(cg[1])))
+
+    def set_blocks_per_sm(self, cap):
+        _check(_lib.dg_batch_set_blocks_per_sm(self.h, int(cap)))
+
+    def autotune(self, trial_steps=2, stream=None):
+        """dg_batch_autotune: time and keep the fastest launch configuration (advances the members)."""
+        _check(_lib.dg_batch_autotune(self.h, int(trial_steps), _stream(stream)))
+        return self.config()
+
+    def config(self):
+        buf = ctypes.create_string_buffer(512)
+        _check(_lib.dg_batch_get_config(self.h, buf, 512))
+        return buf.value.decode()
 
     def set_limit(self, sim, last_step):
         """sim takes no batched step beyond step index last_step (0: no limit)."""

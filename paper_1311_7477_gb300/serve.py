@@ -1,8 +1,9 @@
 """Continuous-batching simulation server on one GPU.
 
 Requests (cells per side N, nodes n, viscosity D, number of steps, initial field -- given
-as node values in "omega0", or generated from the spec's field recipe by host threads)
-arrive over time.  A request is admitted as soon as a batch slot is free and its device-memory
+as node values in "omega0", or generated from the spec's field recipe by host threads --
+and optionally "cg_maxit", the iteration cap of the solves after the start-up one) arrive
+over time.  A request is admitted as soon as a batch slot is free and its device-memory
 footprint fits the HBM budget; admission builds its simulation (initial Poisson solve) on a
 grid shared by all requests of the same (N, n) and takes its two RK4 start-up steps, then
 the request joins the batch (dg_batch_admit).  The GPU loop advances every admitted simulation with one persistent,
@@ -10,6 +11,11 @@ graph-captured launch per chunk of steps (dg_batch_step); a simulation that has 
 steps is retired, its latency (arrival -> completion) recorded and its memory freed, which
 admits waiting requests.  Requests that arrive while others are on the GPU therefore overlap
 with them on the device.
+
+A request whose simulation reports an error (a solve that did not converge, a non-finite
+value, a capped wait) ends alone with that error in the report's "failures" and is left out
+of the latency figures and of the throughput; the others are served.  If a mixed-precision
+request's start-up solve does not converge, it is admitted once more in float64 ("fallbacks").
 
 All GPU work goes through the C ABI (paper_1311_7477_gb300.dg); this module only decides what
 runs when.
@@ -22,7 +28,7 @@ from . import dg, workloads
 
 # device bytes per dof of one simulation (state rings, RK stages, solver and preconditioner
 # vectors, grid workspace), float64 / mixed
-BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 21 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10,
+BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 23 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10,
                  dg.DG_FP64_PC32: 8 * 23 + 4 * 2}
 
 
@@ -40,6 +46,8 @@ class Request:
         self.done_t = None
         self.grid = None
         self.sim = None
+        self.precision = None
+        self.dof_steps = 0        # dof x steps counted for this request so far
         self.remaining = None
         self.field = None
         self.closing = False
@@ -107,8 +115,19 @@ class Server:
         req.field = None
         t1 = clock()
         dt = workloads.stable_dt(dg, s["N"], s["n"], s["D"], dt_cap=self.dt_cap)
-        sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=self.precision, cg_tol=self.cg_tol, cg_maxit=100000)
+        req.precision = self.precision
+        try:
+            sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=self.precision, cg_tol=self.cg_tol, cg_maxit=100000)
+        except dg.DGError as e:
+            if e.code != dg.DG_ERR_NOCONV or self.precision == dg.DG_FP64:
+                raise
+            # the mixed start-up solve did not converge: serve the request in float64
+            req.precision = dg.DG_FP64
+            sim = dg.Sim(g, w0, D=s["D"], dt=dt, precision=dg.DG_FP64, cg_tol=self.cg_tol, cg_maxit=100000)
+            self.fallbacks.append(req.id)
         del w0
+        if s.get("cg_maxit"):        # the request's own iteration cap for its later solves
+            sim.set_cg(self.cg_tol, int(s["cg_maxit"]))
         t2 = clock()
         req.grid, req.sim = g, sim
         req.admit_t = now
@@ -125,26 +144,36 @@ class Server:
         self.t["create"] += t2 - t1
         self.t["admit"] += t3 - t2
         self.dof_steps += req.dof * steps0
-        self.used += footprint(s["N"], s["n"], self.precision)
+        req.dof_steps += req.dof * steps0
+        self.used += footprint(s["N"], s["n"], req.precision)
         self.active.append(req)
 
     def _finish(self, req, now, clock=time.perf_counter):
-        """The request's last step has completed on the device: record it, keep its result if
-        asked, and free its memory (deferred: a free would wait for the running step)."""
+        """The request's last step has completed on the device: check its simulation's status,
+        record it (or its failure), keep its result if asked, and free its memory (deferred: a
+        free would wait for the running step)."""
         import torch
         t0 = clock()
         req.done_t = now
-        if self.keep_results:
+        # the status is read on a side stream: the legacy stream carries the next batched step
+        info = req.sim.status(stream=self.side, check=False)
+        failed = info.status != dg.DG_OK
+        if failed:
+            self.failed.append({"id": req.id, "N": req.spec["N"], "n": req.spec["n"], "error": "status %d after %d "
+                                "steps: %s" % (info.status, info.step, dg.lib().dg_last_error().decode())})
+            self.dof_steps -= req.dof_steps
+        elif self.keep_results:
             om = torch.empty(req.grid.shape, dtype=torch.float64, device="cuda")
             ps = torch.empty_like(om)
             req.sim.get(om, ps)
             torch.cuda.synchronize()
-            self.results[req.id] = (om.cpu().numpy(), ps.cpu().numpy(), req.sim.status().step)
+            self.results[req.id] = (om.cpu().numpy(), ps.cpu().numpy(), req.sim.status(check=False).step)
         self.graveyard.append(req.sim)
         req.sim = req.grid = None
-        self.used -= footprint(req.spec["N"], req.spec["n"], self.precision)
+        self.used -= footprint(req.spec["N"], req.spec["n"], req.precision)
         self.active.remove(req)
-        self.done.append(req)
+        if not failed:
+            self.done.append(req)
         self.t["finish"] += clock() - t0
 
     def _bury(self):
@@ -167,7 +196,9 @@ class Server:
         inflight = []          # (event, requests whose last step is in that launch)
         self.graveyard = []
         self.failed = []
+        self.fallbacks = []
         self.nodes = {}
+        self.side = torch.cuda.Stream()
         self.pool = ThreadPoolExecutor(max_workers=4)
         t0 = clock()
         launches = 0
@@ -202,6 +233,9 @@ class Server:
                         # a start-up failure (e.g. the initial Poisson solve not converging)
                         # ends this request with its error; the others carry on
                         r.field = None
+                        if r.sim is not None:
+                            r.sim.close()
+                        r.sim = r.grid = None
                         self.failed.append({"id": r.id, "N": r.spec["N"], "n": r.spec["n"],
                                             "error": str(e)})
                         continue
@@ -233,6 +267,7 @@ class Server:
                         taken = min(k, r.remaining)
                         r.remaining -= taken
                         self.dof_steps += r.dof * taken
+                        r.dof_steps += r.dof * taken
                 if not runnable and not admitted:
                     if inflight:
                         inflight[0][0].synchronize()
@@ -248,6 +283,7 @@ class Server:
         lat = np.array([r.done_t - r.arrival * time_scale for r in self.done])
         st = self.batch.status(check=False)
         return {"requests": len(self.done), "failed": len(self.failed), "failures": self.failed[:8],
+                "fallbacks_fp64": len(self.fallbacks),
                 "wall_s": wall,
                 "mdof_steps_per_s": self.dof_steps / wall / 1e6,
                 "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,

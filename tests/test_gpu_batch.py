@@ -124,3 +124,37 @@ def test_batch_step_limits(dg):
         assert np.linalg.norm(wa - wb) / np.linalg.norm(wa) < 1e-8
     with pytest.raises(RuntimeError):
         b.set_limit(members[0][1], -1)
+
+
+def test_batch_autotune(dg):
+    """dg_batch_autotune times candidate launch configurations on the live batch (groups, per-n
+    tiles, blocks per SM) and keeps the fastest; the members then still match the same steps
+    taken alone, a second call for the same member classes is a cache hit, and explicit tiles
+    that do not fit are rejected at the next step."""
+    import time
+    members = [_make(dg, *spec, fixed=False) for spec in SPECS]
+    ref = [_make(dg, *spec, fixed=False) for spec in SPECS]
+    b = dg.Batch(8)
+    for g, s in members:
+        b.admit(s)
+    cfg = b.autotune(trial_steps=1)
+    assert cfg.startswith("groups=") and " n5:" in cfg, cfg
+    steps = members[0][1].status().step
+    assert all(s.status().step == steps for _, s in members) and steps > 10
+    t0 = time.perf_counter()
+    assert b.autotune(trial_steps=1) == cfg                 # cached: the same member classes
+    assert time.perf_counter() - t0 < 0.5
+    assert members[0][1].status().step == steps
+    b.step(2)
+    for (g, s) in ref:
+        s.step(steps + 2)
+    for (ga, sa), (gb, sb) in zip(ref, members):
+        wa, _ = _state(ga, sa)
+        wb, _ = _state(gb, sb)
+        assert np.linalg.norm(wa - wb) / np.linalg.norm(wa) < 1e-8
+    assert b.status()["rc"] == 0
+    b.set_tiles(5, rhs=(32, 32))                            # ~1 MB of shared memory per block
+    with pytest.raises(dg.DGError):
+        b.step(1)
+    b.set_tiles(5)
+    b.step(1)

@@ -85,6 +85,12 @@ def test_bracket_parity(dg, Nx, Ny, n, Lx, Ly):
     S = bracket_scale(o, f, h)
     err = rel_l2(got, ref, S)
     assert err < 1e-12, err
+    if Nx > 1 and Ny > 1:
+        # the plain relative error against ||J|| meets the same bar; on grids of one cell in a
+        # direction the periodic neighbour is the cell itself, J is a near-total cancellation
+        # of its parts (for n = 2 it vanishes identically) and only the scaled bound applies
+        plain = rel_l2(got, ref)
+        assert plain < 1e-12, plain
     # the integral constraints of Eqs. average1-3 hold for the GPU result too
     scale = S / np.sqrt(got.size) * np.abs(f).max() * Lx * Ly
     for w in (np.ones_like(f), f, h):
@@ -284,7 +290,12 @@ def test_full_size_shear_layer_sampled(dg):
     # bracket over the whole field
     J = torch.empty(shape, dtype=torch.float64, device="cuda")
     dg.dg_bracket(g, bufs[1], bufs[0], J)
-    assert rel_l2(host(J), o.bracket(ps, om), bracket_scale(o, ps, om)) < 1e-12
+    Jref = o.bracket(ps, om)
+    # relative to the rounding scale only: the shear layer's J is a near cancellation (psi of
+    # size 1 against omega_y of size 400, the layers nearly steady), and both the oracle and the
+    # kernel round its products at eps times that scale, amplified by |D| = rho_D / h ~ 1100
+    # (plain relative L2 of the two about 6e-11 here); the state after the step meets 1e-12 below
+    assert rel_l2(host(J), Jref, bracket_scale(o, ps, om)) < 1e-12
     # one AB3 update of omega from this state
     sim.step(1)
     om1 = torch.empty(shape, dtype=torch.float64, device="cuda")
@@ -306,6 +317,7 @@ def test_bracket_parts_parity(dg, parts):
     Jpp, Jpx, Jxp = o.bracket_parts(f, h)
     ref = {1: Jpp, 2: Jpx, 4: Jxp, 3: Jpp + Jpx, 7: (Jpp + Jpx + Jxp) / 3.0}[parts]
     assert rel_l2(host(J), ref, bracket_scale(o, f, h)) < 1e-12
+    assert rel_l2(host(J), ref) < 1e-12
 
 
 def test_table2_on_the_gpu():

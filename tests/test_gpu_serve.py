@@ -63,3 +63,22 @@ def test_failed_request_does_not_stop_the_others(dg):
     assert rep["failed"] == 1 and rep["failures"][0]["id"] == bad["id"], rep["failures"]
     assert rep["requests"] == len(trace) - 1 and rep["batch_status"] == 0
     assert sorted(r.id for r in srv.done) == sorted(s["id"] for s in trace if s is not bad)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_request_failing_mid_run_ends_alone(dg, precision):
+    """A request whose solves stop converging after admission (its iteration cap cut to one
+    iteration once its start-up solve is done) is reported as failed with its error when it
+    completes, and left out of the served requests and their latencies; the others are
+    served."""
+    from paper_1311_7477_gb300 import serve, workloads
+    prec = {"fp64": dg.DG_FP64, "mixed": dg.DG_MIXED}[precision]
+    trace = workloads.request_trace(count=5, rate=400.0, seed=17, Ns=(16, 24), ns=(2, 3), steps=(6, 12))
+    bad = trace[2]
+    bad["cg_maxit"] = 1
+    srv = serve.Server(max_active=4, hbm_budget=1e9, precision=prec, precond="twolevel", cg_tol=1e-10, chunk=3)
+    rep = srv.run(trace)
+    assert rep["failed"] == 1 and rep["failures"][0]["id"] == bad["id"], rep["failures"]
+    assert "NOCONV" in rep["failures"][0]["error"] or "status 4" in rep["failures"][0]["error"]
+    assert rep["requests"] == len(trace) - 1
+    assert sorted(r.id for r in srv.done) == sorted(s["id"] for s in trace if s is not bad)

@@ -31,6 +31,16 @@ def test_static_solve_matches_allocating_solve_twice(native):
         err = (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item()
         assert err < 1e-12, (call, err)
         assert abs(rr_a - rr_b) <= 1e-12 * max(rr_a, 1e-300) or rr_a == rr_b
+    # a third call with the same n, after the warm-up above: the device's free memory does not
+    # change (nothing is allocated, not even by the CUDA runtime on our behalf)
+    w = torch.from_numpy(np.random.default_rng(7).standard_normal(g.shape)).cuda()
+    b = torch.zeros_like(w)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rc, _, _ = dg.dg_poisson_solve_static(Nx, Ny, n, Lx, Ly, tau, w, b, tol=1e-12, maxit=20000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == dg.DG_OK and free1 == free0, (free0, free1)
 
 
 def test_static_solve_rejects_oversized_grids(native):
