@@ -209,8 +209,8 @@ def oracle_sample(wl, cg_sample_iters=4, precond="twolevel", cells=SAMPLE_CELLS,
 
 
 def oracle_iters_per_step(name, precond="twolevel"):
-    path = os.path.join(ROOT, "tests", "golden", "cg_iterations_shear512_n4_%s.json" % precond)
-    if name == "shear512_n4" and os.path.exists(path):
+    path = os.path.join(ROOT, "tests", "golden", "cg_iterations_%s_%s.json" % (name, precond))
+    if os.path.exists(path):
         d = json.load(open(path))
         if d.get("ab3_iters_mean"):
             return float(d["ab3_iters_mean"]), "the oracle's own CG iterations per AB3 step on this workload"
@@ -357,7 +357,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-steps-scale", type=float, default=0.02)
-    ap.add_argument("--serve-max-cells", type=int, default=512)
+    ap.add_argument("--serve-max-cells", type=int, default=1024)
     ap.add_argument("--serve-groups", type=int, default=0, help="block groups of the batch (0: automatic)")
     ap.add_argument("--batch-compare-fp64", action="store_true",
                     help="batch64: also run the ensemble in float64 and compare each member")
@@ -519,6 +519,7 @@ def main():
                 entry["roofline"] = {"kernel": "mixed_cg_kernel", "bound": "hbm", "achieved": gbs,
                                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                                      "peak_source": peak_src,
+                                     "traffic": measured_traffic("cg_kernel", args.workload, mname),
                                      "bytes_per_dof": "16 + 32 (sweeps + 1) + 32 x inner iterations"}
             modes[mname] = entry
             ms_.close()
@@ -794,9 +795,9 @@ def run_batch(args):
 
 def run_serve(args):
     """The served workload: Poisson arrivals at 20 requests/s (seed 7), cells per side in
-    {64,...,--serve-max-cells} (powers of two; 512 by default), n in {3,4,5}, D log-uniform, random-phase or shear-layer
-    fields; step counts U{100..2000} scaled by --serve-steps-scale (the unscaled trace is about
-    an hour of GPU work)."""
+    {64,...,--serve-max-cells} (powers of two; 1024 by default), n in {3,4,5}, D log-uniform,
+    random-phase or shear-layer fields; step counts U{100..2000} scaled by --serve-steps-scale
+    (the unscaled trace is about an hour of GPU work)."""
     import torch
     from paper_1311_7477_gb300 import build as _build
     _build.build()
@@ -834,6 +835,7 @@ def run_serve(args):
                        "n": [3, 4, 5], "steps_scale": args.serve_steps_scale, "groups": args.serve_groups,
                        "precision": {0: "fp64", 1: "mixed", 2: "mixed64", 3: "fp64pc32"}[prec], "cg_preconditioner": args.precond},
             "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
+            "failed_requests": rep["failed"], "fallbacks_fp64": rep["fallbacks_fp64"],
             "served": rep, "field_generation_s_before_clock": t_gen}
     print(json.dumps(line))
 

@@ -47,6 +47,10 @@ extern "C" {
 #define DG_PRECOND_JACOBI 0    /* W^-1: the inverse diagonal mass matrix (default)          */
 #define DG_PRECOND_TWOLEVEL 1  /* cell block solves + DFT coarse solve on cell averages    */
 
+/* ---- boundary conditions (Sec. 3, Sec. 4.2) ---------------------------------------- */
+#define DG_BC_PERIODIC 0   /* periodic in x and y (the default)                             */
+#define DG_BC_DIRICHLET 1  /* homogeneous Dirichlet on all four sides (see dg_grid_create_bc) */
+
 /* ---- bracket variants of the time stepper (Sec. 6.2, Figures 1-2) ------------------- */
 #define DG_BRACKET_ARAKAWA 0  /* J = (J++ + J+x + Jx+) / 3 of Eq. J: conserves V, E, Omega      */
 #define DG_BRACKET_NAIVE 1    /* J++ alone: the straightforward discretisation the paper        */
@@ -100,6 +104,19 @@ int dg_ref_tables(int n, double tau, double* out, int out_len);
  * DG_ERR_NOMEM, DG_ERR_CUDA.
  */
 int dg_grid_create(dg_grid** g, int Nx, int Ny, int n, double Lx, double Ly, double tau);
+/*
+ * dg_grid_create_bc -- dg_grid_create with the boundary condition bc: DG_BC_PERIODIC, or
+ * DG_BC_DIRICHLET (homogeneous Dirichlet, the fields zero outside [0,Lx] x [0,Ly]).  With
+ * Dirichlet boundaries the derivative's numerical flux on a boundary face is the boundary
+ * value, 0 (Sec. 3; the first and last cells' own blocks 1/2 (D - D^T) + 1/2 L and
+ * 1/2 (D - D^T) - 1/2 R -- the reading that reproduces Table 2's Dirichlet row); the LDG
+ * Laplacian takes u^ = 0 on the boundary faces and a penalty (1/h) u^2 on the left face of
+ * each line (Sec. 6 names no boundary treatment); A is then symmetric positive definite, so
+ * the Poisson solve takes b = W omega without removing the mean.  Dirichlet grids need
+ * tau = 0 and the W^-1 preconditioner.  Errors as dg_grid_create, and DG_ERR_ARG for an
+ * unknown bc or tau != 0 with Dirichlet.
+ */
+int dg_grid_create_bc(dg_grid** g, int Nx, int Ny, int n, double Lx, double Ly, double tau, int bc);
 int dg_grid_destroy(dg_grid* g);
 
 /* Number of values of one field: Nx*Ny*n*n (0 if g is NULL). */
@@ -129,7 +146,8 @@ int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
  * preconditioner B + P A_c^+ P^T -- B the exact inverse of every cell's diagonal block of
  * A, P the prolongation of cell values to the cell's nodes, A_c = P^T A P the Galerkin
  * coarse operator, inverted (constant mode dropped) by a 2D DFT of the cell grid; the
- * solution is returned with zero W-mean.  Errors: DG_ERR_ARG.
+ * solution is returned with zero W-mean.  Errors: DG_ERR_ARG (also for DG_PRECOND_TWOLEVEL on
+ * a Dirichlet grid: its coarse solve is a periodic DFT).
  */
 int dg_grid_set_precond(dg_grid* g, int kind);
 

@@ -11,9 +11,13 @@ namespace {
 
 template <typename T, int N>
 void fill_op(Op1D<T, N>& o, const double M[kMaxN][kMaxN], const double* a, const double* r, const double* d,
-             const double* s) {
+             const double* s, const double Mf[kMaxN][kMaxN] = nullptr, const double* af = nullptr,
+             const double* sf = nullptr) {
   for (int i = 0; i < N; ++i) {
     for (int j = 0; j < N; ++j) o.M[i][j] = T(M[i][j]);
+    for (int j = 0; j < N; ++j) o.Mf[i][j] = T(Mf ? Mf[i][j] : M[i][j]);
+    o.af[i] = T(af ? af[i] : a[i]);
+    o.sf[i] = T(sf ? sf[i] : s[i]);
     o.a[i] = T(a[i]);
     o.r[i] = T(r[i]);
     o.d[i] = T(d[i]);
@@ -21,7 +25,8 @@ void fill_op(Op1D<T, N>& o, const double M[kMaxN][kMaxN], const double* a, const
   }
 }
 
-// Builds the 2D operator tables from the dimensionless per-n tables (Sec. 4.2 / Sec. 6):
+// Builds the 2D operator tables from the dimensionless per-n tables (Sec. 4.2 / Sec. 6)
+// (the LDG operators' Mf: the first cell's own block at a Dirichlet boundary, A1first):
 //   d/dx   = C0/hx, lifts muR/hx and -muL/hx on the traces lL . u_{c+1}, lR . u_{c-1};
 //   -Delta = W^-1 A (x-part: w^-1 A1cc / hx^2, w^-1 betaA / hx^2 on lL . u_{c+1},
 //            w^-1 lL / hx^2 on betaA . u_{c-1});
@@ -37,7 +42,7 @@ Ops2D<T, N> make_ops(const RefTables& t, double hx, double hy) {
   const double hs[2] = {hx, hy};
   for (int dir = 0; dir < 2; ++dir) {
     const double h = hs[dir], h2 = h * h;
-    double M[kMaxN][kMaxN], a[kMaxN], r[kMaxN], d[kMaxN], s[kMaxN];
+    double M[kMaxN][kMaxN], a[kMaxN], r[kMaxN], d[kMaxN], s[kMaxN], Mf[kMaxN][kMaxN], af[kMaxN], sf[kMaxN];
     // central derivative
     for (int i = 0; i < N; ++i) {
       for (int j = 0; j < N; ++j) M[i][j] = t.C0[i][j] / h;
@@ -50,21 +55,27 @@ Ops2D<T, N> make_ops(const RefTables& t, double hx, double hy) {
     // symmetrically scaled LDG stiffness
     for (int i = 0; i < N; ++i) {
       for (int j = 0; j < N; ++j) M[i][j] = rw[i] * t.A1cc[i][j] * rw[j] / h2;
+      for (int j = 0; j < N; ++j) Mf[i][j] = rw[i] * t.A1first[i][j] * rw[j] / h2;
       a[i] = rw[i] * t.betaA[i] / h2;
       r[i] = rw[i] * t.lL[i];
       d[i] = rw[i] * t.lL[i] / h2;
       s[i] = rw[i] * t.betaA[i];
+      af[i] = rw[i] * t.betaFirst[i] / h2;
+      sf[i] = rw[i] * t.betaFirst[i];
     }
-    fill_op<T, N>(dir == 0 ? O.kx : O.ky, M, a, r, d, s);
+    fill_op<T, N>(dir == 0 ? O.kx : O.ky, M, a, r, d, s, Mf, af, sf);
     // -Delta_h = W^-1 A
     for (int i = 0; i < N; ++i) {
       for (int j = 0; j < N; ++j) M[i][j] = t.A1cc[i][j] / (wh[i] * h2);
+      for (int j = 0; j < N; ++j) Mf[i][j] = t.A1first[i][j] / (wh[i] * h2);
       a[i] = t.betaA[i] / (wh[i] * h2);
       r[i] = t.lL[i];
       d[i] = t.lL[i] / (wh[i] * h2);
       s[i] = t.betaA[i];
+      af[i] = t.betaFirst[i] / (wh[i] * h2);
+      sf[i] = t.betaFirst[i];
     }
-    fill_op<T, N>(dir == 0 ? O.lx : O.ly, M, a, r, d, s);
+    fill_op<T, N>(dir == 0 ? O.lx : O.ly, M, a, r, d, s, Mf, af, sf);
   }
   for (int a = 0; a < N; ++a)
     for (int b = 0; b < N; ++b) {
@@ -184,8 +195,10 @@ double ahat_row_bound(const Ops2D<double, N>& O) {
 // with n >= 4, 1024^2 with n >= 3 on [0, 2 pi]^2) the inner solves switch to the double-float
 // apply when a refinement sweep stalls (dg_grid_set_compensated_apply overrides the choice).
 template <int N>
-bool precise_apply_needed(const Ops2D<double, N>& O, double Lx, double Ly) {
-  const double lam_min = std::min(std::pow(2.0 * M_PI / Lx, 2), std::pow(2.0 * M_PI / Ly, 2));
+bool precise_apply_needed(const Ops2D<double, N>& O, double Lx, double Ly, int bc) {
+  const double lam_min = bc == DG_BC_PERIODIC
+                             ? std::min(std::pow(2.0 * M_PI / Lx, 2), std::pow(2.0 * M_PI / Ly, 2))
+                             : std::pow(M_PI / Lx, 2) + std::pow(M_PI / Ly, 2);
   return std::ldexp(ahat_row_bound<N>(O), -24) / lam_min > 0.05;
 }
 
@@ -197,7 +210,7 @@ void build_ops(dg_grid* g) {
   new (g->ops.x) Ops2D<df, N>(x);
   new (g->ops.k) OpsK<df, N>(OpsK<df, N>{x.kx, x.ky});
   const Ops2D<double, N>& Od = *reinterpret_cast<const Ops2D<double, N>*>(g->ops.d);
-  g->precise_auto = precise_apply_needed<N>(Od, g->Lx, g->Ly) ? 2 : 0;
+  g->precise_auto = precise_apply_needed<N>(Od, g->Lx, g->Ly, g->bc) ? 2 : 0;
   g->precise_apply = g->precise_auto;
   const double f = std::ldexp(ahat_row_bound<N>(Od), -52);
   g->floor2 = f * f;
@@ -419,8 +432,14 @@ int dg_ref_tables(int n, double tau, double* out, int out_len) {
 }
 
 int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, double tau) {
+  return dg_grid_create_bc(gp, Nx, Ny, n, Lx, Ly, tau, DG_BC_PERIODIC);
+}
+
+int dg_grid_create_bc(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, double tau, int bc) {
   if (!gp) return fail(DG_ERR_ARG, "g is NULL");
   *gp = nullptr;
+  if (bc != DG_BC_PERIODIC && bc != DG_BC_DIRICHLET) return fail(DG_ERR_ARG, "unknown boundary condition %d", bc);
+  if (bc == DG_BC_DIRICHLET && tau != 0.0) return fail(DG_ERR_ARG, "Dirichlet grids take no jump penalty (tau = 0)");
   if (n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
   if (Nx < 1 || Ny < 1) return fail(DG_ERR_ARG, "Nx, Ny must be >= 1");
   if ((long long)Nx * Ny * n * n > (1ll << 31)) return fail(DG_ERR_ARG, "grid too large");
@@ -436,6 +455,7 @@ int dg_grid_create(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly, do
   g->hx = Lx / Nx;
   g->hy = Ly / Ny;
   g->tau = tau;
+  g->bc = bc;
   build_ref_tables(n, tau, &g->rt);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -487,6 +507,8 @@ int dg_grid_get_compensated_apply(const dg_grid* g) { return g ? g->precise_appl
 int dg_grid_set_precond(dg_grid* g, int kind) {
   if (!g) return fail(DG_ERR_ARG, "g is NULL");
   if (kind != DG_PRECOND_JACOBI && kind != DG_PRECOND_TWOLEVEL) return fail(DG_ERR_ARG, "unknown preconditioner %d", kind);
+  if (kind == DG_PRECOND_TWOLEVEL && g->bc != DG_BC_PERIODIC)
+    return fail(DG_ERR_ARG, "the two-level preconditioner's coarse DFT solve needs a periodic grid");
   g->precond = kind;
   return DG_OK;
 }
@@ -589,6 +611,7 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
   A.psi_out = psi;
   A.tol2 = tol * tol;
   A.floor2 = g->floor2;
+  A.keep_mean = g->bc;
   A.maxit = fixed_iters > 0 ? std::max(maxit, fixed_iters) : maxit;
   A.fixed_iters = fixed_iters;
   A.sumW = g->Lx * g->Ly;
@@ -658,6 +681,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
     A.floor2 = g->floor2;
+    A.keep_mean = g->bc;
     A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
     A.fixed_iters = s->fixed_iters;
     A.sumW = g->Lx * g->Ly;
@@ -674,6 +698,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
     A.floor2 = g->floor2;
+    A.keep_mean = g->bc;
     A.tol_in2 = s->tol_in * s->tol_in;
     A.max_sweeps = s->max_sweeps;
     A.maxit_in = s->maxit;
@@ -692,6 +717,7 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
     A.floor2 = g->floor2;
+    A.keep_mean = g->bc;
     A.maxit = s->fixed_iters > 0 ? std::max(s->maxit, s->fixed_iters) : s->maxit;
     A.fixed_iters = s->fixed_iters;
     A.sumW = g->Lx * g->Ly;
@@ -838,7 +864,7 @@ namespace {
 // Layout of a dg_sim_save file: this header, then six arrays of Nx Ny n^2 float64 values in the
 // cell-blocked node order (omega^k, sqrt(W) psi^k, sqrt(W) psi^{k-1}, R^{k-1}, R^{k-2},
 // R^{k-3}); little-endian, as written by the host.
-const char kSimMagic[8] = {'D', 'G', 'S', 'I', 'M', '0', '0', '1'};
+const char kSimMagic[8] = {'D', 'G', 'S', 'I', 'M', '0', '0', '2'};
 struct SimFileHeader {
   char magic[8];
   int32_t Nx, Ny, n, precision;
@@ -846,8 +872,9 @@ struct SimFileHeader {
   int32_t max_sweeps, precond;
   int64_t step;
   double Lx, Ly, tau, D, dt, tol, tol_in;
+  int32_t bc, reserved;
 };
-static_assert(sizeof(SimFileHeader) == 112, "file header layout");
+static_assert(sizeof(SimFileHeader) == 120, "file header layout");
 
 // A simulation with all its buffers allocated and no state yet (step 0, rings at rest).
 int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double cg_tol, int cg_maxit) {
@@ -1117,6 +1144,7 @@ int dg_sim_save(dg_sim* s, const char* path, void* stream) {
   h.fixed_iters = s->fixed_iters;
   h.max_sweeps = s->max_sweeps;
   h.precond = g->precond;
+  h.bc = g->bc;
   h.step = s->step;
   h.Lx = g->Lx;
   h.Ly = g->Ly;
@@ -1157,9 +1185,9 @@ int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
     return fail(DG_ERR_IO, "%s is not a simulation file of this version", path);
   }
   if (h.Nx != g->Nx || h.Ny != g->Ny || h.n != g->n || h.Lx != g->Lx || h.Ly != g->Ly || h.tau != g->tau ||
-      h.precond != g->precond) {
+      h.precond != g->precond || h.bc != g->bc) {
     std::fclose(f);
-    return fail(DG_ERR_ARG, "the grid (size, n, domain, tau, preconditioner) differs from the saved one");
+    return fail(DG_ERR_ARG, "the grid (size, n, domain, tau, preconditioner, boundaries) differs from the saved one");
   }
   if (h.K < 1 || h.K > 4 || h.step < 0 || (h.bracket != DG_BRACKET_ARAKAWA && h.bracket != DG_BRACKET_NAIVE) ||
       h.fixed_iters < 0 || h.max_sweeps < 1 || !(h.tol_in > 0.0 && h.tol_in < 1.0)) {
@@ -1407,6 +1435,7 @@ BatchSim make_batch_sim(const dg_batch* bt, dg_sim* s) {
   b.ops_df = g->d_opsx;
   b.ops_k = g->d_opsk;
   b.precise_apply = g->precise_apply;
+  b.keep_mean = g->bc;
   for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
   for (int i = 0; i < 3; ++i) b.psi[i] = s->psi[i];
   for (int i = 0; i < 4; ++i) b.R[i] = s->R[i];

@@ -21,6 +21,11 @@ template <typename T, int N>
 struct Op1D {
   T M[N][N];
   T a[N], r[N], d[N], s[N];
+  // the first cell of a line at a Dirichlet boundary (LDG operators; the derivatives keep the
+  // periodic values and handle the boundary through ghost traces): own block, lift of the
+  // right neighbour's trace, and the vector of its own trace seen by the second cell
+  T Mf[N][N];
+  T af[N], sf[N];
 };
 
 template <typename T, int N>
@@ -44,6 +49,7 @@ struct Geom {
   int Nx, Ny;          // cells
   int TX, TY;          // tile (cells)
   int tilesX, tilesY;
+  int bc;              // 0: periodic, 1: homogeneous Dirichlet (zero outside the domain)
 };
 
 // One tile of cells and its one-cell halo ring in shared memory: box cell (br, bc) holds
@@ -88,8 +94,13 @@ __device__ __forceinline__ void stage_box(const Geom& G, const TileBox& B, T* sU
     const bool rowhalo = (br == 0) || (br == BHe - 1);
     const bool colhalo = (bc == 0) || (bc == BWe - 1);
     if (rowhalo && colhalo && !corners) continue;
-    const int cy = wrap_index(B.ty0 + br - 1, G.Ny);
-    const int cx = wrap_index(B.tx0 + bc - 1, G.Nx);
+    const int gy = B.ty0 + br - 1, gx = B.tx0 + bc - 1;
+    if (G.bc && (gy < 0 || gy >= G.Ny || gx < 0 || gx >= G.Nx)) {  // Dirichlet: zero outside
+      sU[(br * B.BW + bc) * (NN + 1) + k] = T(0);
+      continue;
+    }
+    const int cy = wrap_index(gy, G.Ny);
+    const int cx = wrap_index(gx, G.Nx);
     const size_t g = ((size_t)cy * G.Nx + cx) * NN + k;
     sU[(br * B.BW + bc) * (NN + 1) + k] = load(g, k, !(rowhalo || colhalo));
   }
@@ -164,28 +175,91 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
   }
 }
 
-// (Op_x u) at node (a, b) of box cell lc, using the staged field and its x-line traces.
+// (Op_x u) at node (a, b) of box cell lc, using the staged field and its x-line traces; first:
+// the cell is the first of its line at a Dirichlet boundary (own block Mf).
 template <typename T, int N>
 __device__ __forceinline__ T op_x_at(const T* sU, const T* tXR, const T* tXL, const Op1D<T, N>& o,
-                                     int lc, int a, int b) {
+                                     int lc, int a, int b, bool first = false) {
   const T* u = sU + lc * (N * N + 1) + a * N;
-  T acc = o.a[b] * tXR[(lc + 1) * N + a];
+  const T* Mrow = first ? o.Mf[b] : o.M[b];
+  T acc = (first ? o.af[b] : o.a[b]) * tXR[(lc + 1) * N + a];
   acc = fma(o.d[b], tXL[(lc - 1) * N + a], acc);
 #pragma unroll
-  for (int j = 0; j < N; ++j) acc = fma(o.M[b][j], u[j], acc);
+  for (int j = 0; j < N; ++j) acc = fma(Mrow[j], u[j], acc);
   return acc;
 }
 
 // (Op_y u) at node (a, b) of box cell lc (the c+1 neighbour in y is one box row up).
 template <typename T, int N>
 __device__ __forceinline__ T op_y_at(const T* sU, const T* tYR, const T* tYL, const Op1D<T, N>& o,
-                                     int lc, int BW, int a, int b) {
+                                     int lc, int BW, int a, int b, bool first = false) {
   const T* u = sU + lc * (N * N + 1) + b;
-  T acc = o.a[a] * tYR[(lc + BW) * N + b];
+  const T* Mrow = first ? o.Mf[a] : o.M[a];
+  T acc = (first ? o.af[a] : o.a[a]) * tYR[(lc + BW) * N + b];
   acc = fma(o.d[a], tYL[(lc - BW) * N + b], acc);
 #pragma unroll
-  for (int j = 0; j < N; ++j) acc = fma(o.M[a][j], u[j * N], acc);
+  for (int j = 0; j < N; ++j) acc = fma(Mrow[j], u[j * N], acc);
   return acc;
+}
+
+// Homogeneous Dirichlet boundaries for the LDG operators: the trace that the second cell of a
+// line sees of the first one uses the first cell's own vector sf (line_traces wrote s . u).
+// Run after line_traces (and a block synchronisation) on Dirichlet grids only.
+template <typename T, int N>
+__device__ __forceinline__ void dirichlet_first_traces(const TileBox& B, const T* sUx, const T* sUy,
+                                                       const Op1D<T, N>& ox, const Op1D<T, N>& oy, T* tXL, T* tYL) {
+  constexpr int NN = N * N;
+  const int nx = B.tx0 == 0 ? B.TYe * N : 0;   // x-lines of the tile's first column
+  const int ny = B.ty0 == 0 ? B.TXe * N : 0;   // y-lines of the tile's first row
+  for (int i = threadIdx.x; i < nx + ny; i += blockDim.x) {
+    if (i < nx) {
+      const int ry = i / N, line = i - (i / N) * N;
+      const int lc = (ry + 1) * B.BW + 1;
+      const T* u = sUx + lc * (NN + 1) + line * N;
+      T tl = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) tl = fma(ox.sf[j], u[j], tl);
+      tXL[lc * N + line] = tl;
+    } else {
+      const int ii = i - nx;
+      const int rx = ii / N, line = ii - (ii / N) * N;
+      const int lc = B.BW + rx + 1;
+      const T* u = sUy + lc * (NN + 1) + line;
+      T tl = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) tl = fma(oy.sf[j], u[j * N], tl);
+      tYL[lc * N + line] = tl;
+    }
+  }
+}
+
+// Homogeneous Dirichlet boundaries for the central-flux derivative (Sec. 3: the flux on a
+// boundary face is the boundary value, f^ = 0): the ghost cell beyond a boundary face gets the
+// negated trace of the boundary cell on that face, so that the average flux there vanishes.
+// Overwrites the traces of the ghost cells of the tile's lines (x-lines of rows [y0, y1),
+// y-lines of columns [x0, x1), as line_traces computed them with the same `full`).
+template <typename T, int N>
+__device__ __forceinline__ void dirichlet_ghost_traces(const Geom& G, const TileBox& B, T* tXR, T* tXL, T* tYR,
+                                                       T* tYL, bool full) {
+  const int y0 = full ? -1 : 0, y1 = full ? B.TYe + 1 : B.TYe;
+  const int x0 = full ? -1 : 0, x1 = full ? B.TXe + 1 : B.TXe;
+  const bool left = B.tx0 == 0, right = B.tx0 + B.TXe == G.Nx;
+  const bool bottom = B.ty0 == 0, top = B.ty0 + B.TYe == G.Ny;
+  const int nx = (y1 - y0) * N, ny = (x1 - x0) * N;
+  for (int i = threadIdx.x; i < nx + ny; i += blockDim.x) {
+    if (i < nx) {
+      const int ry = i / N + y0, line = i - (i / N) * N;
+      const int row = (ry + 1) * B.BW;
+      if (left) tXL[(row + 0) * N + line] = -tXR[(row + 1) * N + line];
+      if (right) tXR[(row + B.TXe + 1) * N + line] = -tXL[(row + B.TXe) * N + line];
+    } else {
+      const int ii = i - nx;
+      const int rx = ii / N + x0, line = ii - (ii / N) * N;
+      const int col = rx + 1;
+      if (bottom) tYL[(0 * B.BW + col) * N + line] = -tYR[(1 * B.BW + col) * N + line];
+      if (top) tYR[((B.TYe + 1) * B.BW + col) * N + line] = -tYL[(B.TYe * B.BW + col) * N + line];
+    }
+  }
 }
 
 // ---- reductions ------------------------------------------------------------------------

@@ -145,6 +145,7 @@ struct PcTables {
 struct dg_grid {
   int Nx, Ny, n;
   double Lx, Ly, hx, hy, tau;
+  int bc = 0;  // DG_BC_PERIODIC or DG_BC_DIRICHLET
   RefTables rt;
   int rTY, rTX, cTY, cTX;
   int num_sms;
@@ -204,6 +205,7 @@ inline Geom geom_of(const dg_grid* g, int TY, int TX) {
   G.TX = std::min(TX, g->Nx);
   G.tilesX = (g->Nx + G.TX - 1) / G.TX;
   G.tilesY = (g->Ny + G.TY - 1) / G.TY;
+  G.bc = g->bc;
   return G;
 }
 

@@ -16,6 +16,14 @@
 namespace dgk {
 
 constexpr int kThreads = 256;
+// Threads of a standalone RHS block: its tile's staging (up to about 190 KB at n = 5) leaves
+// room for one or two blocks per SM, so the block itself must carry the SM's warps (measured on
+// the 1024^2, n = 5 step: 6.56 / 5.47 / 5.07 ms per RHS with 256 / 512 / 1024 threads; on
+// 512^2, n = 4: 1.01 / 0.88 / 1.12 ms).
+template <int N>
+__host__ __device__ constexpr int rhs_threads() {
+  return N == 5 ? 1024 : 512;
+}
 
 // Copies an operator table (a kernel parameter or a global array) to shared memory: the
 // solves index it with per-thread node numbers, which shared memory serves without the
@@ -129,6 +137,12 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   line_traces<T, N>(B, sOm, sOm, C.dx, C.dy, tOxR, tOxL, tOyR, tOyL, true);
   if (A.visc != 0.0) line_traces<T, N>(B, sOm, sOm, C.lx, C.ly, tLxR, tLxL, tLyR, tLyL, false);
   __syncthreads();
+  if (G.bc) {  // Dirichlet: f^ = 0 on the boundary faces of the derivatives; LDG first cells
+    dirichlet_ghost_traces<T, N>(G, B, tPxR, tPxL, tPyR, tPyL, true);
+    dirichlet_ghost_traces<T, N>(G, B, tOxR, tOxL, tOyR, tOyL, true);
+    if (A.visc != 0.0) dirichlet_first_traces<T, N>(B, sOm, sOm, C.lx, C.ly, tLxL, tLyL);
+    __syncthreads();
+  }
 
   // S2: f_x, g_x on rows [-1, TYe] x cols [0, TXe); f_y, g_y on rows [0, TYe) x cols [-1, TXe].
   {
@@ -202,6 +216,10 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   // S4: traces of h1 along x and of h2 along y (reusing the psi trace arrays).
   line_traces<T, N>(B, sFy, sFx, C.dx, C.dy, tPxR, tPxL, tPyR, tPyL, false);
   __syncthreads();
+  if (G.bc) {
+    dirichlet_ghost_traces<T, N>(G, B, tPxR, tPxL, tPyR, tPyL, false);
+    __syncthreads();
+  }
 
   // S5: J = (J++ + D_x h1 + D_y h2) / 3 = (J++ + J+x + Jx+) / 3, the viscous term and the update.
   const T third = nparts == 3 ? T(1.0 / 3.0) : T(1);
@@ -220,7 +238,9 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
     }
     T R = -J;
     if (A.visc != 0.0) {
-      const T lap = op_x_at<T, N>(sOm, tLxR, tLxL, C.lx, lc, a, b) + op_y_at<T, N>(sOm, tLyR, tLyL, C.ly, lc, BW, a, b);
+      const bool fx = G.bc && B.tx0 + rx == 0, fy = G.bc && B.ty0 + ry == 0;
+      const T lap = op_x_at<T, N>(sOm, tLxR, tLxL, C.lx, lc, a, b, fx) +
+                    op_y_at<T, N>(sOm, tLyR, tLyL, C.ly, lc, BW, a, b, fy);
       R = fma(-T(A.visc), lap, R);  // + D Delta_h omega, since -Delta_h = lx + ly
     }
     double incr = A.c_new * double(R);
@@ -232,7 +252,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+__global__ void __launch_bounds__(rhs_threads<N>()) rhs_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
                                                       const __grid_constant__ RhsArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   rhs_tile<T, N>(stage_table(C, smem_raw), G, A, blockIdx.x, smem_raw + table_bytes<Ops2D<T, N>>());
@@ -266,13 +286,18 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__
   __syncthreads();
   line_traces<T, N>(B, sU, sU, ox, oy, tXR, tXL, tYR, tYL, false);
   __syncthreads();
+  if (G.bc) {
+    dirichlet_first_traces<T, N>(B, sU, sU, ox, oy, tXL, tYL);
+    __syncthreads();
+  }
   const int nin = B.TYe * B.TXe * NN;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
     const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
     const int lc = (ry + 1) * B.BW + rx + 1;
     const int a = k / N, b = k - (k / N) * N;
-    const T q = op_x_at<T, N>(sU, tXR, tXL, ox, lc, a, b) + op_y_at<T, N>(sU, tYR, tYL, oy, lc, B.BW, a, b);
+    const bool fx = G.bc && B.tx0 + rx == 0, fy = G.bc && B.ty0 + ry == 0;
+    const T q = op_x_at<T, N>(sU, tXR, tXL, ox, lc, a, b, fx) + op_y_at<T, N>(sU, tYR, tYL, oy, lc, B.BW, a, b, fy);
     const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
     y[g] = mode == 0 ? double(q * C.sw[k]) : -double(q);
   }
@@ -436,6 +461,10 @@ __device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int t
   __syncthreads();
   line_traces<T, N>(B, X.sU, X.sU, C.kx, C.ky, X.tXR, X.tXL, X.tYR, X.tYL, false);
   __syncthreads();
+  if (G.bc) {
+    dirichlet_first_traces<T, N>(B, X.sU, X.sU, C.kx, C.ky, X.tXL, X.tYL);
+    __syncthreads();
+  }
   const int nin = B.TYe * B.TXe * NN;
   if constexpr (sizeof(T) == 4 && kThreads % NN == 0) {
     // float32: every node a thread visits is node k = threadIdx.x mod n^2 of its cell, so the
@@ -457,25 +486,53 @@ __device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int t
       const T* uy = X.sU + lc * (NN + 1) + b;
       T qx = xa * X.tXR[(lc + 1) * N + a];
       qx = fma(xd, X.tXL[(lc - 1) * N + a], qx);
-#pragma unroll
-      for (int j = 0; j < N; ++j) qx = fma(mx[j], ux[j], qx);
       T qy = ya * X.tYR[(lc + B.BW) * N + b];
       qy = fma(yd, X.tYL[(lc - B.BW) * N + b], qy);
+      if (G.bc && ((B.tx0 == 0 && rx == 0) || (B.ty0 == 0 && ry == 0))) {  // a Dirichlet boundary cell
+        const bool fx = B.tx0 + rx == 0, fy = B.ty0 + ry == 0;
+        const T* Mx = fx ? C.kx.Mf[b] : C.kx.M[b];
+        const T* My = fy ? C.ky.Mf[a] : C.ky.M[a];
+        qx = (fx ? C.kx.af[b] : xa) * X.tXR[(lc + 1) * N + a];
+        qx = fma(xd, X.tXL[(lc - 1) * N + a], qx);
+        qy = (fy ? C.ky.af[a] : ya) * X.tYR[(lc + B.BW) * N + b];
+        qy = fma(yd, X.tYL[(lc - B.BW) * N + b], qy);
 #pragma unroll
-      for (int j = 0; j < N; ++j) qy = fma(my[j], uy[j * N], qy);
+        for (int j = 0; j < N; ++j) qx = fma(Mx[j], ux[j], qx);
+#pragma unroll
+        for (int j = 0; j < N; ++j) qy = fma(My[j], uy[j * N], qy);
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) qx = fma(mx[j], ux[j], qx);
+#pragma unroll
+        for (int j = 0; j < N; ++j) qy = fma(my[j], uy[j * N], qy);
+      }
       const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
       out(g, k, X.sU[lc * (NN + 1) + k], qx + qy);
     }
   } else {
-    for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-      const int c = i / NN, k = i - (i / NN) * NN;
-      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
-      const int lc = (ry + 1) * B.BW + rx + 1;
-      const int a = k / N, b = k - (k / N) * N;
-      const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
-                  op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
-      const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
-      out(g, k, X.sU[lc * (NN + 1) + k], q);
+    if (!G.bc) {
+      for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+        const int c = i / NN, k = i - (i / NN) * NN;
+        const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+        const int lc = (ry + 1) * B.BW + rx + 1;
+        const int a = k / N, b = k - (k / N) * N;
+        const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
+                    op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b);
+        const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+        out(g, k, X.sU[lc * (NN + 1) + k], q);
+      }
+    } else {  // Dirichlet: the first cell of a line takes its own blocks (Op1D::Mf, af)
+      for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+        const int c = i / NN, k = i - (i / NN) * NN;
+        const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+        const int lc = (ry + 1) * B.BW + rx + 1;
+        const int a = k / N, b = k - (k / N) * N;
+        const bool fx = B.tx0 + rx == 0, fy = B.ty0 + ry == 0;
+        const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b, fx) +
+                    op_y_at<T, N>(X.sU, X.tYR, X.tYL, C.ky, lc, B.BW, a, b, fy);
+        const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
+        out(g, k, X.sU[lc * (NN + 1) + k], q);
+      }
     }
   }
   __syncthreads();
@@ -905,6 +962,7 @@ struct CgArgs {
   int maxit, fixed_iters;
   double sumW;
   int cluster;          // launched as one thread-block cluster (cluster barriers)
+  int keep_mean;        // homogeneous Dirichlet: A is definite, b = sqrt(W) omega (no mean removed)
 };
 
 // Dynamic shared memory of the persistent solves: [Bt (with the preconditioner)] then one
@@ -970,7 +1028,7 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
   // P0: W-mean of omega, in two passes (the second removes the rounding left by the first,
   // so that b carries no rounding-sized component along the kernel of A).
   T wbar = T(0);
-  if (A.rhs == nullptr) {
+  if (A.rhs == nullptr && !A.keep_mean) {
     for (int pass = 0; pass < 2; ++pass) {
       T s = T(0);
       for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
@@ -1093,6 +1151,7 @@ struct MixedArgs {
   // until a refinement sweep after the second reduces the residual by less than a factor 100
   // (too inexact on this problem's smoothest modes), double-float from then on
   int precise_apply;
+  int keep_mean;       // homogeneous Dirichlet: b = sqrt(W) omega (no mean removed)
 };
 
 // The operator tables a mixed solve stages in shared memory: float64 (residuals), float32
@@ -1169,7 +1228,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   int flags = 0, sweeps = 0;
   long long inner = 0;
   double rr = 0.0, bb = 0.0, wbar = 0.0, rr_prev = -1.0;
-  for (int mp = 0; mp < 2; ++mp) {  // two-pass W-mean, as in cg_kernel
+  for (int mp = 0; mp < (A.keep_mean ? 0 : 2); ++mp) {  // two-pass W-mean, as in cg_kernel
     double s = 0.0;
     for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
       s = fma(Cd.wq[i % NN], A.omega[i] - wbar, s);
@@ -1311,6 +1370,7 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
 struct BatchSim {
   int n, precision, precond;       // precision: 0 float64, 1 mixed (double-float RHS), 2 mixed (float64 RHS)
   int precise_apply;               // mixed: the inner solve applies Ahat in double-float
+  int keep_mean;                   // homogeneous Dirichlet grid: no mean removed from omega
   Geom Gr, Gc;                     // tiles of the RHS and of the solve
   const void* ops_d;               // device copy of Ops2D<double, n>
   const void* ops_f;               // device copy of Ops2D<float, n>
@@ -1424,6 +1484,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.status = S.status;
     A.tol2 = S.tol2;
     A.floor2 = S.floor2;
+    A.keep_mean = S.keep_mean;
     A.maxit = S.fixed_iters > 0 ? max(S.maxit, S.fixed_iters) : S.maxit;
     A.fixed_iters = S.fixed_iters;
     A.sumW = S.sumW;
@@ -1453,6 +1514,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.status = S.status;
     A.tol2 = S.tol2;
     A.floor2 = S.floor2;
+    A.keep_mean = S.keep_mean;
     A.tol_in2 = S.tol_in2;
     A.max_sweeps = S.max_sweeps;
     A.maxit_in = S.maxit;

@@ -11,7 +11,7 @@ int launch_rhs(const dg_grid* g, const RhsArgs<T>& A, cudaStream_t st) {
   const Geom G = geom_of(g, g->rTY, g->rTX);
   const size_t smem = table_bytes<Ops2D<T, N>>() + rhs_smem_values<T, N>(G.TY, G.TX) * sizeof(T);
   if (int rc = set_smem(rhs_kernel<T, N>, smem)) return rc;
-  rhs_kernel<T, N><<<G.tilesX * G.tilesY, kThreads, smem, st>>>(ops_of<T, N>(g), G, A);
+  rhs_kernel<T, N><<<G.tilesX * G.tilesY, rhs_threads<N>(), smem, st>>>(ops_of<T, N>(g), G, A);
   CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

@@ -124,6 +124,24 @@ int build_ref_tables(int n, double tau, RefTables* t) {
   }
   std::memcpy(t->A1cc, A1, sizeof(A1));
   std::memcpy(t->betaA, beta, sizeof(beta));
+
+  // Dirichlet first cell: G0' = B T^ (-D^T) F (the left-face term -L dropped: u^ = 0 there).
+  Mat G0d{};
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Dm[i][j] = -D[j][i];
+  matmul(n, BT, Dm, tmp);
+  matmul(n, tmp, F, G0d);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += G0d[k][i] * wh[k] * G0d[k][j];
+      t->A1first[i][j] = s + kDirichletPenalty * t->lL[i] * t->lL[j];
+    }
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += G0d[k][i] * wh[k] * liftR[k];
+    t->betaFirst[i] = s;
+  }
   return 0;
 }
 

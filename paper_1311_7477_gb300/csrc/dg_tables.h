@@ -20,7 +20,17 @@ struct RefTables {
   //   h * (A1 u)_c = A1cc u_c + betaA (lL . u_{c+1}) + lL (betaA . u_{c-1})
   double A1cc[kMaxN][kMaxN];
   double betaA[kMaxN];
+  // Homogeneous Dirichlet boundaries: the first cell's diagonal block of A1 (per unit h) when
+  // the forward derivative's flux on the left boundary face is the boundary value u^ = 0
+  // (own block G0' = B T^ (-D^T) F) and the trace is penalised there:
+  //   A1first = G0'^T W G0' + kDirichletPenalty lL lL^T   (no right-neighbour term from the left)
+  double A1first[kMaxN][kMaxN];
+  // ... and its coupling to the second cell: h (A1 u)_0 = A1first u_0 + betaFirst (lL . u_1),
+  // h (A1 u)_1 = ... + lL (betaFirst . u_0), betaFirst = G0'^T W B T^ p(+1)
+  double betaFirst[kMaxN];
 };
+
+constexpr double kDirichletPenalty = 1.0;  // (penalty / h) u(a)^2 on the left boundary face
 
 // Fills t for 1 <= n <= kMaxN and penalty tau >= 0.  Returns 0 on success.
 int build_ref_tables(int n, double tau, RefTables* t);

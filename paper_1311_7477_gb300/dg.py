@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT, DG_ERR_IO = range(8)
 DG_FP64, DG_MIXED, DG_MIXED64, DG_FP64_PC32 = 0, 1, 2, 3
+DG_BC_PERIODIC, DG_BC_DIRICHLET = 0, 1
 DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
 DG_BRACKET_ARAKAWA, DG_BRACKET_NAIVE = 0, 1
 
@@ -53,6 +54,7 @@ def _load():
         "dg_ref_tables_len": (I, [I]),
         "dg_ref_tables": (I, [I, D, PD, I]),
         "dg_grid_create": (I, [PP, I, I, I, D, D, D]),
+        "dg_grid_create_bc": (I, [PP, I, I, I, D, D, D, I]),
         "dg_grid_destroy": (I, [P]),
         "dg_grid_dof": (LL, [P]),
         "dg_grid_nodes": (I, [P, PD, PD, PD]),
@@ -175,12 +177,16 @@ def ref_tables(n, tau=0.0):
 
 
 class Grid:
-    """dg_grid: periodic [0, Lx] x [0, Ly], Nx x Ny cells, n nodes per cell and dimension."""
+    """dg_grid: [0, Lx] x [0, Ly], Nx x Ny cells, n nodes per cell and dimension; periodic
+    (bc="periodic") or homogeneous Dirichlet (bc="dirichlet") boundaries."""
 
-    def __init__(self, Nx, Ny, n, Lx=6.283185307179586, Ly=6.283185307179586, tau=0.0):
+    def __init__(self, Nx, Ny, n, Lx=6.283185307179586, Ly=6.283185307179586, tau=0.0, bc="periodic"):
         h = ctypes.c_void_p()
-        _check(_lib.dg_grid_create(ctypes.byref(h), int(Nx), int(Ny), int(n), float(Lx), float(Ly), float(tau)))
+        code = {"periodic": DG_BC_PERIODIC, "dirichlet": DG_BC_DIRICHLET}[bc]
+        _check(_lib.dg_grid_create_bc(ctypes.byref(h), int(Nx), int(Ny), int(n), float(Lx), float(Ly), float(tau),
+                                      code))
         self.h = h
+        self.bc = bc
         self.Nx, self.Ny, self.n, self.Lx, self.Ly, self.tau = int(Nx), int(Ny), int(n), float(Lx), float(Ly), float(tau)
 
     @property
