@@ -432,10 +432,11 @@ int dg_batch_set_tiles(dg_batch* b, int n, int rhs_ty, int rhs_tx, int cg_ty, in
 int dg_batch_set_blocks_per_sm(dg_batch* b, int cap);
 /*
  * dg_batch_autotune -- picks the batched kernel's launch configuration for the current members
- * by timing it: the number of block groups, then for each n present (the classes with the
- * most degrees of freedom first) the solve tile and the RHS tile, then a cap on blocks per
- * SM; each candidate is timed over trial_steps batched steps (CUDA events on the stream) after
- * one untimed step, and the fastest is kept.  The trial steps are real steps: every member
+ * by timing it, in two rounds of coordinate descent: the number of block groups, then for
+ * each n present (the classes with the most degrees of freedom first) the RHS tile and the
+ * solve tile, then a cap on blocks per SM (a tile's shared memory sets how many blocks fit on
+ * an SM, so the choices interact); each candidate is timed over trial_steps batched steps
+ * (CUDA events on the stream) after one untimed step, and the fastest is kept.  The trial steps are real steps: every member
  * advances (members with a step limit may sit some out, which skews the timings: tune before
  * setting limits).  The result is cached with the members' classes (grid size, n,
  * precision): a later call for the same classes returns at once.  Synchronises the stream.

@@ -1756,9 +1756,23 @@ int dg_batch_autotune(dg_batch* b, int trial_steps, void* stream) {
   };
   float best = 0.f;
   rc = trial(&best);
-  // 1. the number of block groups
   const int ns = (int)b->sims.size();
-  if (!rc) {
+  // the classes of n, the largest total dof first
+  std::vector<std::pair<double, int>> by_n;
+  for (int n = 1; n <= kMaxN; ++n) {
+    double w = 0.0;
+    for (const dg_sim* s : b->sims)
+      if (s->g->n == n) w += (double)ndof_of(s->g);
+    if (w > 0.0) by_n.push_back({w, n});
+  }
+  std::sort(by_n.rbegin(), by_n.rend());
+  static const int kRhsTiles[][2] = {{2, 4}, {4, 4}, {4, 8}, {8, 8}, {8, 16}, {16, 16}};
+  static const int kCgTiles[][2] = {{4, 8}, {8, 8}, {8, 16}, {16, 16}};
+  // Coordinate descent, two rounds (a tile's shared memory sets how many blocks of the whole
+  // batch fit on an SM, so one choice changes what the others are worth): the number of block
+  // groups; per n the RHS tile, then the solve tile; a cap on blocks per SM.  A candidate whose
+  // shared memory does not fit is skipped.
+  for (int round = 0; round < 2 && !rc; ++round) {
     int bestG = b->ngroups_req;
     for (int G : {1, 2, 4, 8, 16, 32}) {
       if (G > ns || G == b->ngroups) continue;
@@ -1771,57 +1785,45 @@ int dg_batch_autotune(dg_batch* b, int trial_steps, void* stream) {
       }
     }
     b->ngroups_req = bestG;
-  }
-  // 2. per n, the largest classes first: the solve tile, then the RHS tile
-  std::vector<std::pair<double, int>> by_n;
-  for (int n = 1; n <= kMaxN; ++n) {
-    double w = 0.0;
-    for (const dg_sim* s : b->sims)
-      if (s->g->n == n) w += (double)ndof_of(s->g);
-    if (w > 0.0) by_n.push_back({w, n});
-  }
-  std::sort(by_n.rbegin(), by_n.rend());
-  static const int kTiles[][2] = {{4, 4}, {4, 8}, {8, 8}, {8, 16}, {16, 16}};
-  for (auto& wn : by_n) {
-    const int n = wn.second;
-    for (int which = 0; which < 2 && !rc; ++which) {
-      int(*tile)[2] = which == 0 ? b->tile_cg : b->tile_rhs;
-      int keep[2] = {tile[n][0], tile[n][1]};
-      for (const auto& t : kTiles) {
-        // double-float / float64 RHS tiles above 8 x 8 cells at n >= 4 exceed the shared memory
-        if (which == 1 && n >= 4 && t[0] * t[1] > 64) continue;
-        if (which == 1 && n == 1 && t[0] * t[1] < 64) continue;
-        tile[n][0] = t[0];
-        tile[n][1] = t[1];
-        float ms = 0.f;
-        const int r = trial(&ms);
-        if (r == DG_ERR_ARG) {  // this tile does not fit: skip it
-          continue;
+    for (auto& wn : by_n) {
+      const int n = wn.second;
+      for (int which = 0; which < 2 && !rc; ++which) {
+        int(*tile)[2] = which == 0 ? b->tile_rhs : b->tile_cg;
+        const int(*cand)[2] = which == 0 ? kRhsTiles : kCgTiles;
+        const int ncand = which == 0 ? 6 : 4;
+        int keep[2] = {tile[n][0], tile[n][1]};
+        for (int c = 0; c < ncand; ++c) {
+          if (cand[c][0] == keep[0] && cand[c][1] == keep[1]) continue;
+          tile[n][0] = cand[c][0];
+          tile[n][1] = cand[c][1];
+          float ms = 0.f;
+          const int r = trial(&ms);
+          if (r == DG_ERR_ARG) continue;  // this tile's shared memory does not fit
+          if ((rc = r)) break;
+          if (ms < best) {
+            best = ms;
+            keep[0] = cand[c][0];
+            keep[1] = cand[c][1];
+          }
         }
-        if ((rc = r)) break;
+        tile[n][0] = keep[0];
+        tile[n][1] = keep[1];
+      }
+    }
+    if (!rc) {
+      int keep = b->bps_cap;
+      for (int cap : {0, 1, 2, 3}) {
+        if (cap == keep) continue;
+        b->bps_cap = cap;
+        float ms = 0.f;
+        if ((rc = trial(&ms))) break;
         if (ms < best) {
           best = ms;
-          keep[0] = t[0];
-          keep[1] = t[1];
+          keep = cap;
         }
       }
-      tile[n][0] = keep[0];
-      tile[n][1] = keep[1];
+      b->bps_cap = keep;
     }
-  }
-  // 3. a cap on resident blocks per SM (fewer, larger groups of blocks can beat full occupancy)
-  if (!rc) {
-    int keep = b->bps_cap;
-    for (int cap : {1, 2, 3}) {
-      b->bps_cap = cap;
-      float ms = 0.f;
-      if ((rc = trial(&ms))) break;
-      if (ms < best) {
-        best = ms;
-        keep = cap;
-      }
-    }
-    b->bps_cap = keep;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
