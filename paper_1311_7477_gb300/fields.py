@@ -53,8 +53,16 @@ def random_phase(X, Y, seed=1, kmax=32, k0=6.0):
     """Sum over integer wave vectors k in a half plane (ky > 0, or ky == 0 and kx > 0),
     0 < |k| <= kmax, of A_k cos(k.x + phi_k), phi_k ~ U[0, 2pi), A_k = sqrt(|k| E(|k|)/pi),
     E(k) = k^4 exp(-(k/k0)^2); rescaled so that the continuous enstrophy
-    1/2 int_{[0,2pi]^2} omega^2 = pi^2 sum A_k^2 equals 1.  Evaluated separably as
-    Re(E_y C E_x^T) over the distinct node coordinates."""
+    1/2 int_{[0,2pi]^2} omega^2 = pi^2 sum A_k^2 equals 1.  X, Y: a tensor mesh (see
+    random_phase_nodes)."""
+    return random_phase_nodes(X[0, :, 0, :], Y[:, 0, :, 0], seed=seed, kmax=kmax, k0=k0)
+
+
+def random_phase_nodes(xn, yn, seed=1, kmax=32, k0=6.0):
+    """random_phase from the node coordinates xn (Nx, n), yn (Ny, n) of a tensor mesh,
+    evaluated separably: with C = A e^{i phi} (ky, kx), the field on node rows ys and node
+    columns xs is Re(E_y C E_x^T), E_y = e^{i ys ky}, E_x = e^{i xs kx}, formed as
+    Re(P) cos(xs kx)^T - Im(P) sin(xs kx)^T with P = E_y C."""
     rng = np.random.default_rng(seed)
     ks = np.arange(-kmax, kmax + 1)
     kx, ky = np.meshgrid(ks, np.arange(0, kmax + 1), indexing="xy")   # shape (kmax+1, 2kmax+1)
@@ -65,13 +73,30 @@ def random_phase(X, Y, seed=1, kmax=32, k0=6.0):
     A = np.sqrt(np.where(keep, kk * E / np.pi, 0.0))
     A = A / np.sqrt(np.pi ** 2 * np.sum(A ** 2))
     C = A * np.exp(1j * phi)                                           # (ky, kx)
-    Ny, Nx, n, _ = X.shape
-    xs = X[0, :, 0, :].reshape(-1)                                     # (Nx*n,)  x of column index cx*n+b
-    ys = Y[:, 0, :, 0].reshape(-1)                                     # (Ny*n,)
-    Ex = np.exp(1j * np.outer(xs, ks))                                 # (Nx*n, 2kmax+1)
-    Ey = np.exp(1j * np.outer(ys, np.arange(0, kmax + 1)))             # (Ny*n, kmax+1)
-    G = np.real(Ey @ C @ Ex.T)                                         # (Ny*n, Nx*n) global [Y][X]
+    xn = np.asarray(xn, dtype=np.float64)
+    yn = np.asarray(yn, dtype=np.float64)
+    Nx, n = xn.shape
+    Ny = yn.shape[0]
+    xs = xn.reshape(-1)                                                # (Nx*n,)  x of column index cx*n+b
+    ys = yn.reshape(-1)                                                # (Ny*n,)
+    P = np.exp(1j * np.outer(ys, np.arange(0, kmax + 1))) @ C          # (Ny*n, 2kmax+1)
+    ph = np.outer(ks, xs)                                              # (2kmax+1, Nx*n)
+    # Re(P E_x^T) = [Re P, -Im P] [cos; sin]: one real product of inner length 2 (2kmax+1)
+    G = np.hstack([P.real, -P.imag]) @ np.vstack([np.cos(ph), np.sin(ph)])   # (Ny*n, Nx*n) [Y][X]
     return G.reshape(Ny, n, Nx, n).transpose(0, 2, 1, 3).copy()
+
+
+def shear_layer_nodes(xn, yn, rho=0.05, delta=0.05):
+    """shear_layer from the node coordinates xn (Nx, n), yn (Ny, n) of a tensor mesh: the
+    field is delta cos x plus a function of y, evaluated on the node lines and broadcast
+    (the same operations per node as shear_layer)."""
+    xn = np.asarray(xn, dtype=np.float64)
+    yn = np.asarray(yn, dtype=np.float64)
+    cx = delta * np.cos(xn)                                            # (Nx, n)
+    lower = 1.0 / (rho * np.cosh((yn - np.pi / 2) / rho) ** 2)         # (Ny, n)
+    upper = 1.0 / (rho * np.cosh((3 * np.pi / 2 - yn) / rho) ** 2)
+    sy = np.where(yn <= np.pi, -lower, upper)       # c - l is c + (-l) exactly
+    return cx[None, :, None, :] + sy[:, None, :, None]
 
 
 def lamb_dipole(X, Y, R=0.1, U=1.0, xc=0.5, yc=0.5):

@@ -80,7 +80,6 @@ def initial_field(dg, grid, spec):
 
 def initial_field_from_nodes(xn, yn, spec):
     from . import fields
-    X, Y = fields.mesh_from_nodes(xn, yn)
     if spec["field"] == "random_phase":
-        return fields.random_phase(X, Y, seed=spec["seed"])
-    return fields.shear_layer(X, Y)
+        return fields.random_phase_nodes(xn, yn, seed=spec["seed"])
+    return fields.shear_layer_nodes(xn, yn)
