@@ -26,10 +26,11 @@ states only that a conjugate gradient method solves it; the details below are a 
 With x0 of W-mean zero all iterates stay W-mean zero, since every update direction
 z = W^{-1} r satisfies sum W z = sum r = 0.
 
-A second preconditioner (a design choice; Sec. 6 names none) is the additive
-two-level one of TwoLevel below: exact solves on every cell plus an exact solve of the
-Galerkin coarse problem on cell averages.  It leaves the solution unchanged and makes the
-iteration count independent of the mesh size.
+Two further preconditioners (design choices; Sec. 6 names none): the additive two-level one
+of TwoLevel below (exact solves on every cell plus an exact solve of the Galerkin coarse
+problem on cell averages), which makes the iteration count independent of the mesh size, and
+Spectral, the exact pseudo-inverse of A on the periodic grid, with which CG converges in one
+iteration.  Neither changes the solution CG converges to.
 """
 import numpy as np
 
@@ -113,6 +114,52 @@ class TwoLevel:
         zb = np.einsum("ij,yxj->yxi", self.Binv, r.reshape(Ny, Nx, n * n)).reshape(r.shape)
         uc = self.coarse_solve(r.sum(axis=(2, 3)))
         return zb + uc[:, :, None, None]
+
+
+class Spectral:
+    """Exact preconditioner  M^{-1} = A^+  (the pseudo-inverse of the Sec. 6 operator, a design
+    choice; Sec. 6 names no preconditioner): on the uniform periodic grid A is block-circulant
+    in cx and in cy, so the 2D DFT over cells splits it into one n^2 x n^2 block per wave
+    vector (kx, ky),
+        A(kx, ky) = W_y (x) A1_x(kx) + A1_y(ky) (x) W_x,   A1(k) = sum_d B_d exp(2 pi i k d / N),
+    B_d the block of the 1D LDG stiffness that couples a cell to its neighbour d cells on
+    (d = -1, 0, 1).  Each block is solved exactly; the block of (0, 0) is singular (its
+    kernel: the constants) and takes its pseudo-inverse.  The result is returned with W-mean
+    zero.  PCG with M^{-1} = A^+ converges in one iteration in exact arithmetic."""
+
+    def __init__(self, ops):
+        g = ops.g
+        n = g.n
+        if getattr(ops, "bc", "periodic") != "periodic":
+            raise ValueError("the spectral preconditioner is built for periodic grids")
+        def symbol(Nc, h):
+            A3 = ldg_matrix_1d(g.t, 3, h, ops.tau)[n:2 * n, :]        # middle cell of a 3-cell line
+            Bm, B0, Bp = A3[:, :n], A3[:, n:2 * n], A3[:, 2 * n:]
+            th = 2.0 * np.pi * np.arange(Nc) / Nc
+            return (B0[None] + np.exp(1j * th)[:, None, None] * Bp[None]
+                    + np.exp(-1j * th)[:, None, None] * Bm[None])          # (Nc, n, n)
+        Ax = symbol(g.Nx, g.hx)
+        Ay = symbol(g.Ny, g.hy)
+        Wx, Wy = np.diag(ops.wx), np.diag(ops.wy)
+        blocks = (np.einsum("ab,xij->xaibj", Wy, Ax)[None]               # W_y (x) A1_x(kx)
+                  + np.einsum("yab,ij->yaibj", Ay, Wx)[:, None])          # A1_y(ky) (x) W_x
+        blocks = blocks.reshape(g.Ny, g.Nx, n * n, n * n)
+        self.inv = np.empty_like(blocks)
+        for ky in range(g.Ny):
+            for kx in range(g.Nx):
+                if kx == 0 and ky == 0:
+                    self.inv[ky, kx] = np.linalg.pinv(blocks[ky, kx], rcond=1e-12, hermitian=True)
+                else:
+                    self.inv[ky, kx] = np.linalg.inv(blocks[ky, kx])
+        self.W = ops.W2
+        self.n = n
+
+    def __call__(self, r):
+        Ny, Nx, n, _ = r.shape
+        rh = np.fft.fft2(r.reshape(Ny, Nx, n * n), axes=(0, 1))
+        zh = np.einsum("yxij,yxj->yxi", self.inv, rh)
+        z = np.fft.ifft2(zh, axes=(0, 1)).real.reshape(r.shape)
+        return z - float(np.sum(self.W * z)) / float(np.sum(self.W))
 
 
 class CGResult:
