@@ -180,7 +180,7 @@ def oracle_sample(wl, cg_sample_iters=4, precond="twolevel", cells=SAMPLE_CELLS,
     from oracle.tables import Grid
     g = Grid(cells, cells, wl["n"])
     ops = Operators(g)
-    M = TwoLevel(ops) if precond == "twolevel" else None
+    M = TwoLevel(ops) if oracle_precond(precond) == "twolevel" else None
     X, Y = g.mesh()
     w = make_field(wl["field"], X, Y)
     psi = 0.01 * np.sin(X) * np.cos(Y)
@@ -208,7 +208,15 @@ def oracle_sample(wl, cg_sample_iters=4, precond="twolevel", cells=SAMPLE_CELLS,
             "cpu_s": t_rhs + t_setup + t_cg}
 
 
+def oracle_precond(precond):
+    """The preconditioner the oracle legs time: the oracle's spectral one stores an n^2 x n^2
+    block inverse per wave vector (about 10 GB at 1024^2 cells, n = 5), so those legs time the
+    two-level one in its place."""
+    return "twolevel" if precond == "spectral" else precond
+
+
 def oracle_iters_per_step(name, precond="twolevel"):
+    precond = oracle_precond(precond)
     path = os.path.join(ROOT, "tests", "golden", "cg_iterations_%s_%s.json" % (name, precond))
     if os.path.exists(path):
         d = json.load(open(path))
@@ -240,7 +248,7 @@ def cpu_baseline(name, wl, native_iters, precond="twolevel", threads=1):
             "sample": ("FP64 NumPy oracle, %d thread(s): %d full AB3 steps (bracket + viscous term + update, "
                        "Poisson setup, %d CG iterations with the %s preconditioner; %s) on a %dx%d-cell "
                        "grid of the same n=%d, field and parameters (%d dof), rate per dof; %.1f s of CPU"
-                       % (threads, s["reps"], kint, precond, ksrc, s["cells"], s["cells"], wl["n"],
+                       % (threads, s["reps"], kint, oracle_precond(precond), ksrc, s["cells"], s["cells"], wl["n"],
                           s["sample_dof"], s["cpu_s"])),
             "parts_s_per_dof": s}
 
@@ -350,7 +358,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64", "fp64pc32"],
                     help="default: fp64 for the single runs, mixed for batch64 and serve")
-    ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel"])
+    ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel", "spectral"])
     ap.add_argument("--no-mixed-compare", action="store_true")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -551,6 +559,12 @@ def main():
     if args.precond == "twolevel":
         flops_iter_i += 2 * n * n + 4 + 2 + 4 * 5 * math.log2(N) / (n * n)
         bytes_iter_i += 2 * 8            # z written and read
+    elif args.precond == "spectral":
+        # real 2D DFT forward and inverse (5 log2(N^2) flop per dof), four n x n complex
+        # transforms of the half spectrum (16 n flop per dof); r read, the spectrum written and
+        # read three times, z written: 8 + 6 * 8 + 8 B per dof (float64 complex, half spectrum)
+        flops_iter_i += 5 * math.log2(N * N) + 16 * n
+        bytes_iter_i += 8 + 6 * 8 + 8
     flops_setup_i = 4 * (n + 4) + 8
     sec = cg_ms_per_launch / 1e3
     fp64 = args.precision in ("fp64", "fp64pc32")
@@ -566,7 +580,7 @@ def main():
             "implementation_count": {"achieved": ach_i, "frac": ach_i / pk,
                                      "flops_per_dof_iter": flops_iter_i, "flops_per_dof_setup": flops_setup_i,
                                      "bytes_per_dof_iter": bytes_iter_i,
-                                     "what": "assembled 1D operators + two-level preconditioner work"},
+                                     "what": "assembled 1D operators + %s preconditioner work" % args.precond},
             "hbm": {"achieved": gbs_m, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs_m / peaks["hbm_gbs"], "peak_source": peak_src},
             "launch_ms": cg_ms_per_launch, "iters_per_launch": it_per_launch,

@@ -46,6 +46,7 @@ extern "C" {
 /* ---- CG preconditioners (Sec. 6 names none; see dg_grid_set_precond) ---------------- */
 #define DG_PRECOND_JACOBI 0    /* W^-1: the inverse diagonal mass matrix (default)          */
 #define DG_PRECOND_TWOLEVEL 1  /* cell block solves + DFT coarse solve on cell averages    */
+#define DG_PRECOND_SPECTRAL 2  /* the exact pseudo-inverse of the periodic operator by DFTs */
 
 /* ---- boundary conditions (Sec. 3, Sec. 4.2) ---------------------------------------- */
 #define DG_BC_PERIODIC 0   /* periodic in x and y (the default)                             */
@@ -146,10 +147,29 @@ int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
  * preconditioner B + P A_c^+ P^T -- B the exact inverse of every cell's diagonal block of
  * A, P the prolongation of cell values to the cell's nodes, A_c = P^T A P the Galerkin
  * coarse operator, inverted (constant mode dropped) by a 2D DFT of the cell grid; the
- * solution is returned with zero W-mean.  Errors: DG_ERR_ARG (also for DG_PRECOND_TWOLEVEL on
- * a Dirichlet grid: its coarse solve is a periodic DFT).
+ * solution is returned with zero W-mean.  DG_PRECOND_SPECTRAL: M^-1 = A^+ itself.  On the
+ * uniform periodic grid the scaled operator W^-1/2 A W^-1/2 = I (x) Kx + Ky (x) I is
+ * block-circulant along both cell indices, so a DFT over the cells reduces each 1D operator
+ * to one n x n Hermitian matrix per wave number (eigen-decomposed on the host, see
+ * dg_spectral_symbol); z = A^+ r is a real 2D DFT of the n^2 node fields, n x n transforms per
+ * wave vector, a division by the eigenvalue sums (the constant mode dropped) and the inverse
+ * transforms.  CG then converges in one iteration in exact arithmetic (two or three in
+ * floating point); the solution is returned with zero W-mean.  Errors: DG_ERR_ARG (also for
+ * DG_PRECOND_TWOLEVEL and DG_PRECOND_SPECTRAL on a Dirichlet grid: both use periodic DFTs).
  */
 int dg_grid_set_precond(dg_grid* g, int kind);
+
+/*
+ * dg_spectral_symbol -- host-only: the symbol of the scaled 1D CG operator (the operator of
+ * Sec. 6 scaled by w^-1/2 on both sides) of a periodic line of N cells of total length L, at
+ * wave number k (0 <= k < N): K(k) = M + e^{i th} a r^T + e^{-i th} d s^T, th = 2 pi k / N, for
+ * (Op u)_c = M u_c + a (r . u_{c+1}) + d (s . u_{c-1}); returns its eigen-decomposition
+ * K = V diag(lam) V^*: lam[n] ascending, V row-major by real (Vre[n*n]) and imaginary (Vim[n*n])
+ * parts, column j the eigenvector of lam[j].  At k = 0 the constant mode's eigenvalue is
+ * returned as exactly 0.  These are the tables of DG_PRECOND_SPECTRAL.
+ * Errors: DG_ERR_ARG.
+ */
+int dg_spectral_symbol(int N, int n, double L, double tau, int k, double* lam, double* Vre, double* Vim);
 
 /*
  * dg_grid_set_compensated_apply -- how the float32 inner solves of DG_MIXED / DG_MIXED64
@@ -224,7 +244,7 @@ int dg_poisson_solve(dg_grid* g, const double* omega, double* psi, double tol, i
  * since creating one allocates.  The paper has no counterpart; this is an interface choice.
  * It takes the grid as plain parameters (Nx, Ny, n, Lx, Ly, tau as in dg_grid_create) and
  * keeps all its scratch (CG vectors, partial sums, barrier and status words) in one
- * file-scope device array of about 2.6 MB that every GPU loading the library holds until
+ * file-scope device array of about 2.8 MB that every GPU loading the library holds until
  * the process exits.  Grids are limited to Nx*Ny*n*n <= 65536 values; larger ones are
  * rejected with DG_ERR_ARG.  It calls no cudaMalloc, cudaFree or other allocating routine.
  * Every call looks up the array's device address on the current device

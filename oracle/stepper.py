@@ -32,14 +32,15 @@ class Simulation:
 
     def __init__(self, ops, omega0, D, dt, tol=1e-12, maxit=100000, K=3,
                  fixed_iters=0, psi0=None, precond="jacobi", bracket="arakawa"):
-        """precond: "jacobi" (W^{-1}) or "twolevel" (solver.TwoLevel); bracket: "arakawa"
+        """precond: "jacobi" (W^{-1}), "twolevel" (solver.TwoLevel) or "spectral"
+        (solver.Spectral); bracket: "arakawa"
         (Eq. J) or "naive" (J^{++} alone)."""
         if bracket not in ("arakawa", "naive"):
             raise ValueError(bracket)
         self.bracket = bracket
         self.ops, self.D, self.dt = ops, float(D), float(dt)
-        from .solver import TwoLevel
-        self.precond = TwoLevel(ops) if precond == "twolevel" else None
+        from .solver import Spectral, TwoLevel
+        self.precond = {"twolevel": TwoLevel, "spectral": Spectral}.get(precond, lambda o: None)(ops)
         self.tol, self.maxit, self.K, self.fixed_iters = float(tol), int(maxit), int(K), int(fixed_iters)
         self.omega = np.array(omega0, dtype=np.float64, copy=True)
         if psi0 is None:

@@ -117,6 +117,8 @@ void free_ws(Workspace& w) {
   cudaFree(w.prcf);
   cudaFree(w.pucf);
   cudaFree(w.pCf);
+  cudaFree(w.pS);
+  cudaFree(w.pSf);
   if (w.host_out) cudaFreeHost(w.host_out);
   w = Workspace{};
 }
@@ -141,16 +143,23 @@ int alloc_ws(Workspace& w, size_t ndof, int grid_cap, bool with_y) {
   return DG_OK;
 }
 
-int alloc_ws_precond(Workspace& w, size_t ncell, bool mixed) {
+// Preconditioner work arrays for a grid of Nx x Ny cells with n nodes per side: the two-level
+// vectors and the spectral preconditioner's spectrum ((Nx/2 + 1) Ny n^2 complex values),
+// float64 and, for the mixed modes, float32.
+int alloc_ws_precond(Workspace& w, int Nx, int Ny, int n, bool mixed) {
+  const size_t ncell = (size_t)Nx * Ny;
+  const size_t nspec = (size_t)(Nx / 2 + 1) * Ny * n * n;
   CUDA_TRY(cudaMalloc(&w.pz, w.ndof * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w.prc, ncell * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w.puc, ncell * sizeof(double)));
   CUDA_TRY(cudaMalloc(&w.pC, ncell * sizeof(Cplx<double>)));
+  CUDA_TRY(cudaMalloc(&w.pS, nspec * sizeof(Cplx<double>)));
   if (mixed) {
     CUDA_TRY(cudaMalloc(&w.pzf, w.ndof * sizeof(float)));
     CUDA_TRY(cudaMalloc(&w.prcf, ncell * sizeof(float)));
     CUDA_TRY(cudaMalloc(&w.pucf, ncell * sizeof(float)));
     CUDA_TRY(cudaMalloc(&w.pCf, ncell * sizeof(Cplx<float>)));
+    CUDA_TRY(cudaMalloc(&w.pSf, nspec * sizeof(Cplx<float>)));
   }
   return DG_OK;
 }
@@ -229,6 +238,14 @@ void free_pc(PcTables& t) {
   cudaFree(t.twyf);
   cudaFree(t.axf);
   cudaFree(t.ayf);
+  cudaFree(t.Vx);
+  cudaFree(t.Vy);
+  cudaFree(t.lx);
+  cudaFree(t.ly);
+  cudaFree(t.Vxf);
+  cudaFree(t.Vyf);
+  cudaFree(t.lxf);
+  cudaFree(t.lyf);
   t = PcTables{};
 }
 
@@ -293,6 +310,79 @@ int upload_tw(int L, Cplx<double>** d, Cplx<float>** f) {
   return DG_OK;
 }
 
+// ---- spectral preconditioner tables -------------------------------------------------------
+
+// The symbol of a scaled 1D CG operator on a periodic line of Nc cells at wave number k,
+// K(k) = M + e^{i th} a r^T + e^{-i th} d s^T with th = 2 pi k / Nc (from (Op u)_c = M u_c +
+// a (r . u_{c+1}) + d (s . u_{c-1}) and u_c = sum_k u^_k e^{i th c}), and its eigen-decomposition
+// K = V diag(lam) V^* (row-major V, column j = eigenvector j, lam ascending).  K is Hermitian
+// because the operator is symmetric; its parts are symmetrised before the decomposition.  At
+// k = 0 the smallest eigenvalue is the constant mode's, rounding-sized: it is set to exactly 0.
+template <int N>
+int spectral_symbol(const Op1D<double, N>& o, int Nc, int k, double* lam, double* Vre, double* Vim) {
+  // in long double: at small k the terms of the symbol cancel to a smallest eigenvalue ~1e-7
+  // of the largest, which float64 would leave with a relative error of ~1e-9
+  using R = long double;
+  const R pi = 3.141592653589793238462643383279502884L;
+  const R th = 2.0L * pi * R(k) / R(Nc);
+  const R c = std::cos(th), sn = std::sin(th);
+  R Kre[N * N], Kim[N * N];
+  for (int b = 0; b < N; ++b)
+    for (int j = 0; j < N; ++j) {
+      Kre[b * N + j] = R(o.M[b][j]) + c * (R(o.a[b]) * R(o.r[j]) + R(o.d[b]) * R(o.s[j]));
+      Kim[b * N + j] = sn * (R(o.a[b]) * R(o.r[j]) - R(o.d[b]) * R(o.s[j]));
+    }
+  for (int b = 0; b < N; ++b)
+    for (int j = b; j < N; ++j) {
+      const R re = 0.5L * (Kre[b * N + j] + Kre[j * N + b]);
+      const R im = 0.5L * (Kim[b * N + j] - Kim[j * N + b]);
+      Kre[b * N + j] = Kre[j * N + b] = re;
+      Kim[b * N + j] = im;
+      Kim[j * N + b] = -im;
+    }
+  if (hermitian_eig(N, Kre, Kim, lam, Vre, Vim)) return fail(DG_ERR_ARG, "eigen-decomposition of the symbol did not converge");
+  if (k == 0) {
+    // the constant mode: zero up to the rounding of the (cancelling) sum of the blocks
+    double big = 0.0;
+    for (int b = 0; b < N; ++b)
+      for (int j = 0; j < N; ++j)
+        big = std::max({big, std::fabs(o.M[b][j]), std::fabs(o.a[b] * o.r[j]), std::fabs(o.d[b] * o.s[j])});
+    if (std::fabs(lam[0]) > 1e-9 * big) return fail(DG_ERR_ARG, "the symbol at k = 0 has no null mode");
+    lam[0] = 0.0;
+  }
+  return DG_OK;
+}
+
+// Vx / lx for kx = 0 .. Nx/2 and Vy / ly for ky = 0 .. Ny - 1 (PrecondArgs), float64 and float32.
+template <int N>
+int build_spectral(dg_grid* g) {
+  const Ops2D<double, N>& O = *reinterpret_cast<const Ops2D<double, N>*>(g->ops.d);
+  PcTables& P = g->pc;
+  auto line = [&](const Op1D<double, N>& o, int Nc, int kcount, Cplx<double>** V, double** lam, Cplx<float>** Vf,
+                  float** lamf) {
+    std::vector<Cplx<double>> vh((size_t)kcount * N * N);
+    std::vector<Cplx<float>> vf((size_t)kcount * N * N);
+    std::vector<double> lh((size_t)kcount * N);
+    for (int k = 0; k < kcount; ++k) {
+      double l[N], vre[N * N], vim[N * N];
+      if (int rc = spectral_symbol<N>(o, Nc, k, l, vre, vim)) return rc;
+      for (int i = 0; i < N * N; ++i) {
+        vh[(size_t)k * N * N + i] = Cplx<double>{vre[i], vim[i]};
+        vf[(size_t)k * N * N + i] = Cplx<float>{float(vre[i]), float(vim[i])};
+      }
+      for (int i = 0; i < N; ++i) lh[(size_t)k * N + i] = l[i];
+    }
+    CUDA_TRY(cudaMalloc(V, vh.size() * sizeof(Cplx<double>)));
+    CUDA_TRY(cudaMemcpy(*V, vh.data(), vh.size() * sizeof(Cplx<double>), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(Vf, vf.size() * sizeof(Cplx<float>)));
+    CUDA_TRY(cudaMemcpy(*Vf, vf.data(), vf.size() * sizeof(Cplx<float>), cudaMemcpyHostToDevice));
+    if (int rc = upload(lam, lh)) return rc;
+    return upload(lamf, lh);
+  };
+  if (int rc = line(O.kx, g->Nx, g->Nx / 2 + 1, &P.Vx, &P.lx, &P.Vxf, &P.lxf)) return rc;
+  return line(O.ky, g->Ny, g->Ny, &P.Vy, &P.ly, &P.Vyf, &P.lyf);
+}
+
 // The cell block A_cc = W_y (x) A1_cc/hx + A1_cc/hy (x) W_x (node index a*n + b), its inverse
 // scaled by sqrt(W) on both sides; the coarse eigenvalues of P^T A P from the 1D cell-average
 // stencil [co, cc, co] (cc = 1^T A1_cc 1, co = (1^T betaA)(1^T lL), per unit h):
@@ -341,6 +431,11 @@ int build_pc(dg_grid* g) {
   if (int rc = upload_tw(g->Ny, &P.twy, &P.twyf)) return rc;
   P.log2x = log2_exact(g->Nx);
   P.log2y = log2_exact(g->Ny);
+  // the spectral tables: their failure (reported by dg_grid_set_precond) leaves the grid usable
+  if (g->bc == DG_BC_PERIODIC) {
+    P.spectral_rc = dispatch_n(n, [&](auto nc) { return build_spectral<decltype(nc)::value>(g); });
+    if (P.spectral_rc == DG_ERR_CUDA || P.spectral_rc == DG_ERR_NOMEM) return P.spectral_rc;
+  }
   return DG_OK;
 }
 
@@ -470,7 +565,7 @@ int dg_grid_create_bc(dg_grid** gp, int Nx, int Ny, int n, double Lx, double Ly,
     return DG_OK;
   });
   int rc = alloc_ws(g->ws, ndof_of(g), co_resident_cap(g), true);
-  if (!rc) rc = alloc_ws_precond(g->ws, (size_t)Nx * Ny, false);
+  if (!rc) rc = alloc_ws_precond(g->ws, Nx, Ny, n, false);
   if (!rc) rc = build_pc(g);
   if (!rc) rc = upload_ops(g);
   if (rc) {
@@ -506,11 +601,29 @@ int dg_grid_get_compensated_apply(const dg_grid* g) { return g ? g->precise_appl
 
 int dg_grid_set_precond(dg_grid* g, int kind) {
   if (!g) return fail(DG_ERR_ARG, "g is NULL");
-  if (kind != DG_PRECOND_JACOBI && kind != DG_PRECOND_TWOLEVEL) return fail(DG_ERR_ARG, "unknown preconditioner %d", kind);
+  if (kind != DG_PRECOND_JACOBI && kind != DG_PRECOND_TWOLEVEL && kind != DG_PRECOND_SPECTRAL)
+    return fail(DG_ERR_ARG, "unknown preconditioner %d", kind);
   if (kind == DG_PRECOND_TWOLEVEL && g->bc != DG_BC_PERIODIC)
     return fail(DG_ERR_ARG, "the two-level preconditioner's coarse DFT solve needs a periodic grid");
+  if (kind == DG_PRECOND_SPECTRAL && g->bc != DG_BC_PERIODIC)
+    return fail(DG_ERR_ARG, "the spectral preconditioner needs a periodic grid");
+  if (kind == DG_PRECOND_SPECTRAL && g->pc.spectral_rc != DG_OK)
+    return fail(DG_ERR_ARG, "the spectral preconditioner's tables could not be built for this grid");
   g->precond = kind;
   return DG_OK;
+}
+
+int dg_spectral_symbol(int N, int n, double L, double tau, int k, double* lam, double* Vre, double* Vim) {
+  if (n < 1 || n > kMaxN) return fail(DG_ERR_ARG, "n = %d outside 1..5", n);
+  if (N < 1 || k < 0 || k >= N || !(L > 0.0) || !(tau >= 0.0)) return fail(DG_ERR_ARG, "bad line or wave number");
+  if (!lam || !Vre || !Vim) return fail(DG_ERR_ARG, "NULL argument");
+  RefTables t;
+  if (build_ref_tables(n, tau, &t)) return fail(DG_ERR_ARG, "table construction failed");
+  return dispatch_n(n, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    const Ops2D<double, NC> O = make_ops<double, NC>(t, L / N, L / N);
+    return spectral_symbol<NC>(O.kx, N, k, lam, Vre, Vim);
+  });
 }
 
 long long dg_grid_dof(const dg_grid* g) { return g ? (long long)ndof_of(g) : 0; }
@@ -911,7 +1024,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
     CUDA_TRY(cudaMalloc(&s->k2, rbytes));
     CUDA_TRY(cudaMalloc(&s->k3, rbytes));
     if (int rc = alloc_ws(s->ws, ndof_of(g), co_resident_cap(g), false)) return rc;
-    if (int rc = alloc_ws_precond(s->ws, (size_t)g->Nx * g->Ny, precision != DG_FP64)) return rc;
+    if (int rc = alloc_ws_precond(s->ws, g->Nx, g->Ny, g->n, precision != DG_FP64)) return rc;
     return (precision == DG_MIXED || precision == DG_MIXED64) ? alloc_ws_mixed(s->ws) : DG_OK;
   };
   if (int rc = alloc_all()) {
@@ -1259,7 +1372,7 @@ int dg_sim_invariants(dg_sim* s, double out[3], void* stream) {
 // framework -- this entry point runs the same persistent CG kernel as dg_poisson_solve but
 // keeps every scratch vector, the per-block partial sums, the grid barrier and the status
 // word in one file-scope __device__ array of fixed size.  Each GPU that loads the library
-// holds that array (about 2.6 MB) until the process exits.
+// holds that array (about 2.8 MB) until the process exits.
 // ---------------------------------------------------------------------------------------
 namespace {
 
@@ -1482,13 +1595,12 @@ size_t batch_smem_for(const dg_batch* b, const dg_sim* s) {
   Geom Gr, Gc;
   batch_geoms(b, g, &Gr, &Gc);
   const int Lmax = std::max(g->Nx, g->Ny);
-  const bool pc = g->precond == DG_PRECOND_TWOLEVEL;
   size_t out = 0;
   dispatch_n(g->n, [&](auto nc) {
     constexpr int N = decltype(nc)::value;
     const size_t rhs = rhs_smem_values<double, N>(Gr.TY, Gr.TX) * sizeof(double);  // double or double-float
-    const size_t sol = s->precision == DG_FP64 ? cg_smem_bytes<double, N>(Gc.TY, Gc.TX, Lmax, pc)
-                                               : mixed_smem_bytes<N>(Gc.TY, Gc.TX, Lmax, pc);
+    const size_t sol = s->precision == DG_FP64 ? cg_smem_bytes<double, N>(Gc.TY, Gc.TX, Lmax, g->precond, pow2_grid(g))
+                                               : mixed_smem_bytes<N>(Gc.TY, Gc.TX, Lmax, g->precond, pow2_grid(g));
     out = batch_ops_bytes<N>() + std::max(rhs, sol);
     return DG_OK;
   });

@@ -59,7 +59,16 @@ struct Geom {
 // lines would hit the same bank).
 struct TileBox {
   int ty0, tx0, TYe, TXe, BW;
+  unsigned mTXe;  // magic_of(TXe): cell c of the tile is in tile row quot(c, mTXe)
 };
+
+// Integer quotients by a divisor d that is fixed for a loop: m = magic_of(d) (once), then
+// quot(c, m) = c / d for 0 <= c with c * d < 2^32 (one multiply-high in place of a division).
+// With m = floor((2^32 - 1) / d) + 1 = (2^32 + e) / d, 0 <= e < d, the product c m / 2^32 is
+// c / d + c e / (d 2^32), and c e < 2^32 keeps the added part below 1/d, so its floor is the
+// quotient.  d = 1 (m would be 2^32) is encoded as m = 0.
+__host__ __device__ __forceinline__ unsigned magic_of(int d) { return d == 1 ? 0u : 0xFFFFFFFFu / unsigned(d) + 1u; }
+__device__ __forceinline__ int quot(int c, unsigned m) { return m ? int(__umulhi(unsigned(c), m)) : c; }
 
 __device__ __forceinline__ int wrap_index(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
@@ -71,6 +80,7 @@ __device__ __forceinline__ TileBox make_box(const Geom& G, int tile) {
   B.TYe = min(G.TY, G.Ny - B.ty0);
   B.TXe = min(G.TX, G.Nx - B.tx0);
   B.BW = G.TX + 2;
+  B.mTXe = magic_of(B.TXe);
   return B;
 }
 
@@ -83,11 +93,12 @@ __device__ __forceinline__ void stage_box(const Geom& G, const TileBox& B, T* sU
   const int BWe = B.TXe + 2, BHe = B.TYe + 2;
   const int rowlen = BWe * NN;
   const int total = BHe * rowlen;
+  const unsigned mrow = magic_of(rowlen);
   // one flat loop over the whole box, so that a thread's loads of several rows are in flight
   // together
 #pragma unroll 4
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int br = i / rowlen;
+    const int br = quot(i, mrow);
     const int j = i - br * rowlen;
     const int bc = j / NN;
     const int k = j - bc * NN;
@@ -121,6 +132,7 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
   const int wx = B.TXe + 2, hx = y1 - y0;   // x-line cells: rows y0..y1-1, cols -1..TXe
   const int wy = x1 - x0, hy = B.TYe + 2;   // y-line cells: rows -1..TYe, cols x0..x1-1
   const int nx = hx * wx * N, ny = hy * wy * N;
+  const unsigned mwx = magic_of(wx), mwy = magic_of(wy);
   // the trace coefficients: in registers for float32 (for float64 the registers are scarcer
   // than the shared-memory issue slots of this FMA-bound path)
   T xr[N], xs[N], yr[N], ys[N];
@@ -136,7 +148,8 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
   for (int i = threadIdx.x; i < nx + ny; i += blockDim.x) {
     if (i < nx) {
       const int c = i / N, line = i - (i / N) * N;
-      const int ry = c / wx + y0, rx = c - (c / wx) * wx - 1;
+      const int cq = quot(c, mwx);
+      const int ry = cq + y0, rx = c - cq * wx - 1;
       const int lc = (ry + 1) * B.BW + rx + 1;
       const T* u = sUx + lc * (NN + 1) + line * N;
       T tr = T(0), tl = T(0);
@@ -155,7 +168,8 @@ __device__ __forceinline__ void line_traces(const TileBox& B, const T* sUx, cons
     } else {
       const int ii = i - nx;
       const int c = ii / N, line = ii - (ii / N) * N;
-      const int ry = c / wy - 1, rx = c - (c / wy) * wy + x0;
+      const int cq = quot(c, mwy);
+      const int ry = cq - 1, rx = c - cq * wy + x0;
       const int lc = (ry + 1) * B.BW + rx + 1;
       const T* u = sUy + lc * (NN + 1) + line;
       T tr = T(0), tl = T(0);
@@ -454,6 +468,127 @@ __device__ __forceinline__ void dft_line(Cplx<T>* s, Cplx<T>* tmp, int L, int lo
 // Position of element j of a line in the shared buffer before dft_line.
 __device__ __forceinline__ int dft_slot(int j, int log2L) {
   return log2L > 0 ? int(__brev(unsigned(j)) >> (32 - log2L)) : j;
+}
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cadd(Cplx<T> a, Cplx<T> b) {
+  return Cplx<T>{a.re + b.re, a.im + b.im};
+}
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> csub(Cplx<T> a, Cplx<T> b) {
+  return Cplx<T>{a.re - b.re, a.im - b.im};
+}
+
+// DFTs of `count` lines of length L held one after another in shared memory (line c at
+// s + c L), computed by the whole block; tw, inverse and the non-power-of-two fallback (a
+// direct sum into tmp[0 .. count L)) as for dft_line.  Power-of-two L: with dif == false the
+// decimation-in-time form of dft_line (bit-reversed input, natural output); with dif == true
+// decimation in frequency (natural input, output in bit-reversed order: element k of the
+// transform at position dft_slot(k, log2L)).  Both take two radix-2 stages per pass.
+template <typename T>
+__device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, int L, int log2L, const Cplx<T>* tw,
+                                          bool inverse, bool dif) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (log2L < 0) {
+    for (int i = tid; i < count * L; i += nth) {
+      const int c = i / L, k = i - c * L;
+      const Cplx<T>* x = s + c * L;
+      T re = T(0), im = T(0);
+      int m = 0;  // (j * k) mod L
+      for (int j = 0; j < L; ++j) {
+        Cplx<T> w = tw[m];
+        if (inverse) w.im = -w.im;
+        const Cplx<T> v = cmul(w, x[j]);
+        re += v.re;
+        im += v.im;
+        m += k;
+        if (m >= L) m -= L;
+      }
+      tmp[i] = Cplx<T>{re, im};
+    }
+    __syncthreads();
+    for (int i = tid; i < count * L; i += nth) s[i] = tmp[i];
+    __syncthreads();
+    return;
+  }
+  if (log2L == 0) return;
+  const int q = L >> 2;  // radix-2^2 butterflies per line and pass
+  if (!dif) {
+    int half = 1, lh = 0;
+    if (log2L & 1) {  // one radix-2 stage (span 1) first
+      const int hl = L >> 1;
+      for (int t = tid; t < count * hl; t += nth) {
+        Cplx<T>* b = s + (t >> (log2L - 1)) * L + 2 * (t & (hl - 1));
+        const Cplx<T> u = b[0], v = b[1];
+        b[0] = cadd(u, v);
+        b[1] = csub(u, v);
+      }
+      __syncthreads();
+      half = 2;
+      lh = 1;
+    }
+    for (; half < L; half <<= 2, lh += 2) {
+      const int s2 = L / (2 * half), s4 = L / (4 * half);
+      for (int t = tid; t < count * q; t += nth) {
+        const int line = t >> (log2L - 2), tt = t & (q - 1);
+        const int grp = tt >> lh, pos = tt & (half - 1);
+        Cplx<T>* b = s + line * L + grp * 4 * half + pos;
+        Cplx<T> w2 = tw[pos * s2], w4 = tw[pos * s4];
+        if (inverse) {
+          w2.im = -w2.im;
+          w4.im = -w4.im;
+        }
+        const Cplx<T> a = b[0], bb = cmul(w2, b[half]);
+        const Cplx<T> c = b[2 * half], d = cmul(w2, b[3 * half]);
+        const Cplx<T> A1 = cadd(a, bb), B1 = csub(a, bb);
+        const Cplx<T> C1 = cmul(w4, cadd(c, d));
+        Cplx<T> D1 = cmul(w4, csub(c, d));
+        D1 = inverse ? Cplx<T>{-D1.im, D1.re} : Cplx<T>{D1.im, -D1.re};  // times -+ i
+        b[0] = cadd(A1, C1);
+        b[2 * half] = csub(A1, C1);
+        b[half] = cadd(B1, D1);
+        b[3 * half] = csub(B1, D1);
+      }
+      __syncthreads();
+    }
+  } else {
+    // spans 2h and h per pass, from 2h = L / 2 down; a last span-1 stage if log2L is odd
+    int h = q, lh = log2L - 2, stages = log2L;
+    for (; stages >= 2; h >>= 2, lh -= 2, stages -= 2) {
+      const int s4 = L / (4 * h), s2 = L / (2 * h);
+      for (int t = tid; t < count * q; t += nth) {
+        const int line = t >> (log2L - 2), tt = t & (q - 1);
+        const int grp = tt >> lh, pos = tt & (h - 1);
+        Cplx<T>* b = s + line * L + grp * 4 * h + pos;
+        Cplx<T> w4 = tw[pos * s4], w2 = tw[pos * s2];
+        if (inverse) {
+          w4.im = -w4.im;
+          w2.im = -w2.im;
+        }
+        const Cplx<T> x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
+        const Cplx<T> y0 = cadd(x0, x2), y1 = cadd(x1, x3);
+        const Cplx<T> y2 = cmul(csub(x0, x2), w4);
+        Cplx<T> y3 = cmul(csub(x1, x3), w4);
+        y3 = inverse ? Cplx<T>{-y3.im, y3.re} : Cplx<T>{y3.im, -y3.re};  // w4^h = -+ i
+        b[0] = cadd(y0, y1);
+        b[h] = cmul(csub(y0, y1), w2);
+        b[2 * h] = cadd(y2, y3);
+        b[3 * h] = cmul(csub(y2, y3), w2);
+      }
+      __syncthreads();
+    }
+    if (stages == 1) {
+      const int hl = L >> 1;
+      for (int t = tid; t < count * hl; t += nth) {
+        Cplx<T>* b = s + (t >> (log2L - 1)) * L + 2 * (t & (hl - 1));
+        const Cplx<T> u = b[0], v = b[1];
+        b[0] = cadd(u, v);
+        b[1] = csub(u, v);
+      }
+      __syncthreads();
+    }
+  }
 }
 
 }  // namespace dgk

@@ -122,6 +122,9 @@ struct Workspace {
   Cplx<double>* pC = nullptr;
   float *pzf = nullptr, *prcf = nullptr, *pucf = nullptr;
   Cplx<float>* pCf = nullptr;
+  // spectrum of the spectral preconditioner, (Nx/2 + 1) x Ny x n x n (float64 and float32)
+  Cplx<double>* pS = nullptr;
+  Cplx<float>* pSf = nullptr;
   SyncState* sync = nullptr;
   SolveStatus* status = nullptr;
   double* inv_part = nullptr;  // 3 * kInvBlocks
@@ -140,6 +143,12 @@ struct PcTables {
   Cplx<float>*twxf = nullptr, *twyf = nullptr;
   float *axf = nullptr, *ayf = nullptr;
   int log2x = -1, log2y = -1;
+  // spectral preconditioner (periodic grids): eigenvectors and eigenvalues of the 1D symbols
+  Cplx<double>*Vx = nullptr, *Vy = nullptr;
+  double *lx = nullptr, *ly = nullptr;
+  Cplx<float>*Vxf = nullptr, *Vyf = nullptr;
+  float *lxf = nullptr, *lyf = nullptr;
+  int spectral_rc = DG_ERR_ARG;  // DG_OK once the spectral tables are built
 };
 
 struct dg_grid {
@@ -151,7 +160,7 @@ struct dg_grid {
   int num_sms;
   OpsHost ops;
   Workspace ws;
-  int precond = 0;  // DG_PRECOND_JACOBI or DG_PRECOND_TWOLEVEL
+  int precond = 0;  // DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL or DG_PRECOND_SPECTRAL
   bool cluster_ok = true;  // small solves may run as one thread-block cluster
   PcTables pc;
   void* d_opsd = nullptr;  // device copies of the operator tables (batched kernel)
@@ -235,12 +244,23 @@ int dispatch_n(int n, F&& f) {
 
 template <typename Kern>
 int set_smem(Kern k, size_t bytes) {
-  if (bytes > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  // above 48 KB of static plus dynamic shared memory a kernel must opt in; our kernels' static
+  // shared memory is well under 16 KB
+  if (bytes > 32 * 1024) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return DG_OK;
 }
 
+// Both cell counts are powers of two (the DFTs run in place, without a second line buffer).
+inline bool pow2_grid(const dg_grid* g) { return g->pc.log2x >= 0 && g->pc.log2y >= 0; }
+
 inline PrecondArgs<double> pc_args(const dg_grid* g, const Workspace& w) {
   PrecondArgs<double> P{};
+  P.kind = g->precond;
+  P.Vx = g->pc.Vx;
+  P.lx = g->pc.lx;
+  P.Vy = g->pc.Vy;
+  P.ly = g->pc.ly;
+  P.S = w.pS;
   P.Bt = g->pc.Bt;
   P.twx = g->pc.twx;
   P.twy = g->pc.twy;
@@ -257,6 +277,12 @@ inline PrecondArgs<double> pc_args(const dg_grid* g, const Workspace& w) {
 
 inline PrecondArgs<float> pc_args_f(const dg_grid* g, const Workspace& w) {
   PrecondArgs<float> P{};
+  P.kind = g->precond;
+  P.Vx = g->pc.Vxf;
+  P.lx = g->pc.lxf;
+  P.Vy = g->pc.Vyf;
+  P.ly = g->pc.lyf;
+  P.S = w.pSf;
   P.Bt = g->pc.Btf;
   P.twx = g->pc.twxf;
   P.twy = g->pc.twyf;

@@ -151,7 +151,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
     for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
       if (i < n1) {
         const int c = i / NN, k = i - (i / NN) * NN;
-        const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
+        const int ry = quot(c, B.mTXe) - 1, rx = c - (ry + 1) * B.TXe;
         const int lc = (ry + 1) * BW + rx + 1;
         const int a = k / N, b = k - (k / N) * N;
         sFx[lc * CS + k] = op_x_at<T, N>(sPsi, tPxR, tPxL, C.dx, lc, a, b);
@@ -179,7 +179,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   const int nin = B.TYe * B.TXe * NN;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
     const int o = ((ry + 1) * BW + rx + 1) * CS + k;
     sJ[o] = prod_diff(sFx[o], sGy[o], sFy[o], sGx[o]);
   }
@@ -202,7 +202,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
       } else {
         const int ii = i - n1;
         const int c = ii / NN, k = ii - (ii / NN) * NN;
-        const int ry = c / B.TXe - 1, rx = c - (c / B.TXe) * B.TXe;
+        const int ry = quot(c, B.mTXe) - 1, rx = c - (ry + 1) * B.TXe;
         const int o = ((ry + 1) * BW + rx + 1) * CS + k;
         if (nparts == 3)
           sFx[o] = prod_diff(sFx[o], sOm[o], sPsi[o], sGx[o]);
@@ -225,7 +225,7 @@ __device__ __forceinline__ void rhs_tile(const Ops2D<T, N>& C, const Geom& G, co
   const T third = nparts == 3 ? T(1.0 / 3.0) : T(1);
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
     const int lc = (ry + 1) * BW + rx + 1;
     const int a = k / N, b = k - (k / N) * N;
     const T dxh1 = op_x_at<T, N>(sFy, tPxR, tPxL, C.dx, lc, a, b);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const __grid_constant__
   const int nin = B.TYe * B.TXe * NN;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     const int c = i / NN, k = i - (i / NN) * NN;
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
     const int lc = (ry + 1) * B.BW + rx + 1;
     const int a = k / N, b = k - (k / N) * N;
     const bool fx = G.bc && B.tx0 + rx == 0, fy = G.bc && B.ty0 + ry == 0;
@@ -360,18 +360,36 @@ constexpr int kMaxRestarts = 20;
 // sqrt(W) r~  (= P^T r),  Bt = diag(sqrt W) A_cc^-1 diag(sqrt W)  (one n^2 x n^2 matrix for
 // every cell), A_c = P^T A P the Galerkin coarse operator on the cells, diagonalised by the
 // 2D DFT with eigenvalues ax[kx] + ay[ky] (constant mode dropped).
+//
+// The spectral preconditioner is M^-1 = Ahat^+ itself.  On the uniform periodic grid
+// Ahat = I (x) Kx + Ky (x) I is block-circulant along both cell indices, so the DFT over cells
+// turns each 1D operator into one n x n Hermitian matrix per wave number,
+// Kx(kx) = M + e^{i th} a r^T + e^{-i th} d s^T (th = 2 pi kx / Nx), diagonalised on the host:
+// Kx(kx) = Vx diag(lx) Vx^*, Ky(ky) = Vy diag(ly) Vy^*.  z~ = Ahat^+ r~ is then: a real DFT
+// along x of the n^2 node fields and Vx^* per (cy, kx, a); a DFT along y, Vy^* per (ky, kx, j),
+// division by ly_i + lx_j (the constant mode, the one pair whose sum is exactly 0, dropped),
+// Vy and the inverse DFT along y; Vx and the inverse real DFT along x.  Three grid-wide phases
+// over the spectrum S[kx][cy][a][j] (kx <= Nx/2).
+enum : int { kPrecondJacobi = 0, kPrecondTwoLevel = 1, kPrecondSpectral = 2 };
+
 template <typename T>
 struct PrecondArgs {
+  int kind;             // kPrecondTwoLevel or kPrecondSpectral
   const T* Bt;          // N^2 x N^2, row-major
   const Cplx<T>* twx;   // exp(-2 pi i m / Nx), m < Nx
   const Cplx<T>* twy;   // exp(-2 pi i m / Ny), m < Ny
   const T* ax;          // coarse eigenvalues: lambda(kx, ky) = ax[kx] + ay[ky]
   const T* ay;
   int log2x, log2y;     // log2 of Nx, Ny when powers of two, else -1 (direct DFT)
-  T* z;                 // cell-block part of z~ (one value per dof)
+  T* z;                 // cell-block part of z~ (two-level) or all of z~ (spectral), one per dof
   T* rc;                // restricted residual (one per cell)
   T* uc;                // coarse correction (one per cell)
   Cplx<T>* C;           // coarse spectrum (Ny x (Nx/2 + 1))
+  const Cplx<T>* Vx;    // spectral: Vx[kx][b][j], kx <= Nx/2 (column j = eigenvector j)
+  const T* lx;          // lx[kx][j]
+  const Cplx<T>* Vy;    // Vy[ky][a][i], ky < Ny
+  const T* ly;          // ly[ky][i]
+  Cplx<T>* S;           // spectrum, (Nx/2 + 1) x Ny x N x N
 };
 
 // Shared memory and synchronisation of one persistent solve.
@@ -480,7 +498,7 @@ __device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int t
     const T xa = C.kx.a[b], xd = C.kx.d[b], ya = C.ky.a[a], yd = C.ky.d[a];
     for (int i = threadIdx.x; i < nin; i += kThreads) {
       const int c = i / NN;
-      const int ry = c / B.TXe, rx = c - ry * B.TXe;
+      const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
       const int lc = (ry + 1) * B.BW + rx + 1;
       const T* ux = X.sU + lc * (NN + 1) + a * N;
       const T* uy = X.sU + lc * (NN + 1) + b;
@@ -513,7 +531,7 @@ __device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int t
     if (!G.bc) {
       for (int i = threadIdx.x; i < nin; i += blockDim.x) {
         const int c = i / NN, k = i - (i / NN) * NN;
-        const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+        const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
         const int lc = (ry + 1) * B.BW + rx + 1;
         const int a = k / N, b = k - (k / N) * N;
         const T q = op_x_at<T, N>(X.sU, X.tXR, X.tXL, C.kx, lc, a, b) +
@@ -524,7 +542,7 @@ __device__ __forceinline__ void cg_tile_apply(const Tab& C, const Geom& G, int t
     } else {  // Dirichlet: the first cell of a line takes its own blocks (Op1D::Mf, af)
       for (int i = threadIdx.x; i < nin; i += blockDim.x) {
         const int c = i / NN, k = i - (i / NN) * NN;
-        const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+        const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
         const int lc = (ry + 1) * B.BW + rx + 1;
         const int a = k / N, b = k - (k / N) * N;
         const bool fx = B.tx0 + rx == 0, fy = B.ty0 + ry == 0;
@@ -596,7 +614,7 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
     for (int j = 0; j < NN; ++j) bk[j] = Bs[j * NN + k];
     for (int i = threadIdx.x; i < nin; i += kThreads) {
       const int c = i / NN;
-      const int ry = c / B.TXe, rx = c - ry * B.TXe;
+      const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
       const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
       const TP* u = su + cell;
       TP zj = TP(0);
@@ -609,7 +627,7 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
   } else {
     for (int i = threadIdx.x; i < nin; i += blockDim.x) {
       const int c = i / NN, k = i - (i / NN) * NN;
-      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+      const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
       const int cell = ((ry + 1) * B.BW + rx + 1) * (NN + 1);
       const TP* u = su + cell;
       TP zj = TP(0);
@@ -622,7 +640,7 @@ __device__ __forceinline__ T pc_cells(const Ops2D<T, N>& C, const Geom& G, const
   }
   const int ncell = B.TYe * B.TXe;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-    const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+    const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
     const TP* u = su + ((ry + 1) * B.BW + rx + 1) * (NN + 1);
     TP v = TP(0);
 #pragma unroll
@@ -727,11 +745,193 @@ __device__ __forceinline__ bool pc_coarse(const Geom& G, const PrecondArgs<T>& P
   return reduce_all(X, acc, ucrc);
 }
 
+// ---- the spectral preconditioner's three phases (see PrecondArgs) -------------------------
+// Units of the row phases: (row pair pr, node row a): rows cy0 = 2 pr, cy1 = 2 pr + 1 travel as
+// one complex line per node column b (real part row cy0, imaginary part row cy1), as in
+// pc_coarse.  Shared memory: N lines of max(Nx, Ny) complex values (twice that for the direct
+// DFT of a length that is not a power of two).
+
+// Phase 1: S[kx][cy][a][j] = sum_b conj(Vx[kx][b][j]) DFT_x(r~[cy, ., a, b])[kx].
+template <typename TP, int N, typename TR>
+__device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondArgs<TP>& P, const TR* r,
+                                                  SolveCtx<TR>& X) {
+  const int Nx = G.Nx, Ny = G.Ny, W = Nx / 2 + 1;
+  Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
+  Cplx<TP>* Lt = L0 + N * Nx;
+  const int units = (Ny + 1) / 2 * N;
+  for (int u = X.vrank; u < units; u += X.vsize) {
+    const int pr = u / N, a = u - pr * N;
+    const int cy0 = 2 * pr, cy1 = cy0 + 1;
+    const bool hasb = cy1 < Ny;
+    for (int i = threadIdx.x; i < Nx * N; i += blockDim.x) {
+      const int cx = i / N, b = i - cx * N;
+      const TP va = TP(__ldcg(r + (((size_t)cy0 * Nx + cx) * N + a) * N + b));
+      const TP vb = hasb ? TP(__ldcg(r + (((size_t)cy1 * Nx + cx) * N + a) * N + b)) : TP(0);
+      L0[b * Nx + dft_slot(cx, P.log2x)] = Cplx<TP>{va, vb};
+    }
+    __syncthreads();
+    fft_lines(L0, Lt, N, Nx, P.log2x, P.twx, false, false);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+      const int km = k == 0 ? 0 : Nx - k;
+      Cplx<TP> A[N], B[N];
+#pragma unroll
+      for (int b = 0; b < N; ++b) {
+        const Cplx<TP> zk = L0[b * Nx + k], zm = L0[b * Nx + km];
+        A[b] = Cplx<TP>{TP(0.5) * (zk.re + zm.re), TP(0.5) * (zk.im - zm.im)};
+        B[b] = Cplx<TP>{TP(0.5) * (zk.im + zm.im), TP(0.5) * (zm.re - zk.re)};
+      }
+      const Cplx<TP>* V = P.Vx + (size_t)k * N * N;
+      Cplx<TP>* Sa = P.S + (((size_t)k * Ny + cy0) * N + a) * N;
+      Cplx<TP>* Sb = P.S + (((size_t)k * Ny + cy1) * N + a) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Cplx<TP> ta{TP(0), TP(0)}, tb{TP(0), TP(0)};
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          const Cplx<TP> v = V[b * N + j];  // conj(v) * x
+          ta.re = fma(v.re, A[b].re, fma(v.im, A[b].im, ta.re));
+          ta.im = fma(v.re, A[b].im, fma(-v.im, A[b].re, ta.im));
+          tb.re = fma(v.re, B[b].re, fma(v.im, B[b].im, tb.re));
+          tb.im = fma(v.re, B[b].im, fma(-v.im, B[b].re, tb.im));
+        }
+        st_cplx(Sa + j, ta);
+        if (hasb) st_cplx(Sb + j, tb);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 2, per unit (kx, j): DFT along y of S[kx][.][a][j] for every a, then per ky
+// t = Vy^* x, t_i *= scale / (ly_i + lx_j) (0 for the constant mode), x = Vy t, inverse DFT.
+template <typename TP, int N, typename TR>
+__device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<TP>& P, SolveCtx<TR>& X) {
+  const int Nx = G.Nx, Ny = G.Ny, W = Nx / 2 + 1;
+  Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
+  Cplx<TP>* Lt = L0 + N * Ny;
+  const TP scale = TP(1) / (TP(Nx) * TP(Ny));
+  for (int u = X.vrank; u < W * N; u += X.vsize) {
+    const int kx = u / N, j = u - kx * N;
+    const Cplx<TP>* Sk = P.S + (size_t)kx * Ny * N * N;
+    for (int i = threadIdx.x; i < Ny * N; i += blockDim.x) {
+      const int cy = i / N, a = i - cy * N;
+      L0[a * Ny + dft_slot(cy, P.log2y)] = ld_cplx(Sk + ((size_t)cy * N + a) * N + j);
+    }
+    __syncthreads();
+    fft_lines(L0, Lt, N, Ny, P.log2y, P.twy, false, false);
+    const TP lxj = P.lx[kx * N + j];
+    for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
+      const Cplx<TP>* V = P.Vy + (size_t)ky * N * N;
+      Cplx<TP> x[N], t[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) x[a] = L0[a * Ny + ky];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        Cplx<TP> acc{TP(0), TP(0)};
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const Cplx<TP> v = V[a * N + i];
+          acc.re = fma(v.re, x[a].re, fma(v.im, x[a].im, acc.re));
+          acc.im = fma(v.re, x[a].im, fma(-v.im, x[a].re, acc.im));
+        }
+        const TP den = P.ly[ky * N + i] + lxj;
+        const TP f = den == TP(0) ? TP(0) : scale / den;
+        t[i] = Cplx<TP>{acc.re * f, acc.im * f};
+      }
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        Cplx<TP> acc{TP(0), TP(0)};
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc = cadd(acc, cmul(V[a * N + i], t[i]));
+        L0[a * Ny + ky] = acc;
+      }
+    }
+    __syncthreads();
+    fft_lines(L0, Lt, N, Ny, P.log2y, P.twy, true, true);
+    Cplx<TP>* Sw = P.S + (size_t)kx * Ny * N * N;
+    for (int i = threadIdx.x; i < Ny * N; i += blockDim.x) {
+      const int cy = i / N, a = i - cy * N;
+      st_cplx(Sw + ((size_t)cy * N + a) * N + j, L0[a * Ny + dft_slot(cy, P.log2y)]);
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 3: z~[cy, ., a, b] = inverse real DFT_x of sum_j Vx[kx][b][j] S[kx][cy][a][j]; returns
+// this block's share of r~ . z~ in acc.
+template <typename TP, int N, typename TR>
+__device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondArgs<TP>& P, const TR* r,
+                                                  SolveCtx<TR>& X, TR& acc) {
+  const int Nx = G.Nx, Ny = G.Ny, W = Nx / 2 + 1;
+  Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
+  Cplx<TP>* Lt = L0 + N * Nx;
+  const int units = (Ny + 1) / 2 * N;
+  for (int u = X.vrank; u < units; u += X.vsize) {
+    const int pr = u / N, a = u - pr * N;
+    const int cy0 = 2 * pr, cy1 = cy0 + 1;
+    const bool hasb = cy1 < Ny;
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+      const Cplx<TP>* V = P.Vx + (size_t)k * N * N;
+      const Cplx<TP>* Sa = P.S + (((size_t)k * Ny + cy0) * N + a) * N;
+      const Cplx<TP>* Sb = P.S + (((size_t)k * Ny + cy1) * N + a) * N;
+      Cplx<TP> ta[N], tb[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        ta[j] = ld_cplx(Sa + j);
+        tb[j] = hasb ? ld_cplx(Sb + j) : Cplx<TP>{TP(0), TP(0)};
+      }
+      const bool mirror = k > 0 && 2 * k != Nx;  // Nx - k is a distinct bin
+#pragma unroll
+      for (int b = 0; b < N; ++b) {
+        Cplx<TP> A{TP(0), TP(0)}, B{TP(0), TP(0)};
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const Cplx<TP> v = V[b * N + j];
+          A = cadd(A, cmul(v, ta[j]));
+          B = cadd(B, cmul(v, tb[j]));
+        }
+        // Z = A + i B at k; at Nx - k the spectra of the real rows are conj(A), conj(B)
+        L0[b * Nx + k] = Cplx<TP>{A.re - B.im, A.im + B.re};
+        if (mirror) L0[b * Nx + Nx - k] = Cplx<TP>{A.re + B.im, B.re - A.im};
+      }
+    }
+    __syncthreads();
+    fft_lines(L0, Lt, N, Nx, P.log2x, P.twx, true, true);
+    for (int i = threadIdx.x; i < Nx * N; i += blockDim.x) {
+      const int cx = i / N, b = i - cx * N;
+      const Cplx<TP> zv = L0[b * Nx + dft_slot(cx, P.log2x)];
+      const size_t g0 = (((size_t)cy0 * Nx + cx) * N + a) * N + b;
+      __stcg(P.z + g0, zv.re);
+      acc = fma(TR(zv.re), __ldcg(r + g0), acc);
+      if (hasb) {
+        const size_t g1 = (((size_t)cy1 * Nx + cx) * N + a) * N + b;
+        __stcg(P.z + g1, zv.im);
+        acc = fma(TR(zv.im), __ldcg(r + g1), acc);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// z~ = Ahat^+ r~ (spectral preconditioner): the three phases and the sum r~ . z~ (in every block).
+template <typename TP, int N, typename TR>
+__device__ __forceinline__ bool pc_spectral(const Geom& G, const PrecondArgs<TP>& P, const TR* r, SolveCtx<TR>& X,
+                                            TR& rz) {
+  spectral_rows_fwd<TP, N, TR>(G, P, r, X);
+  if (!solve_barrier(X)) return false;
+  spectral_cols<TP, N, TR>(G, P, X);
+  if (!solve_barrier(X)) return false;
+  TR acc = TR(0);
+  spectral_rows_inv<TP, N, TR>(G, P, r, X, acc);
+  return reduce_all(X, acc, rz);
+}
+
 // z~ = M^-1 r~ for the residual currently in r; returns r~ . z~ in rz.
 template <typename T, int N, typename TP = T>
 __device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, const PrecondArgs<TP>& P, const T* r,
                                          SolveCtx<T>& X, T& rz) {
   constexpr int NN = N * N;
+  if (P.kind == kPrecondSpectral) return pc_spectral<TP, N, T>(G, P, r, X, rz);
   const int ntiles = G.tilesX * G.tilesY;
   TP* su = pc_stage<T, TP>(X);
   T rzb = T(0);
@@ -740,7 +940,7 @@ __device__ __forceinline__ bool pc_apply(const Ops2D<T, N>& C, const Geom& G, co
     const int nin = B.TYe * B.TXe * NN;
     for (int i = threadIdx.x; i < nin; i += blockDim.x) {
       const int c = i / NN, k = i - (i / NN) * NN;
-      const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+      const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
       const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
       const int o = ((ry + 1) * B.BW + rx + 1) * (NN + 1) + k;
       const T v = __ldcg(r + g);
@@ -778,6 +978,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
   T beta = T(0);
   int cur = 0;
   bool first = true;  // p = z (no previous direction)
+  const bool spec = P && P->kind == kPrecondSpectral;
   if (!P) rz = rr;
   while (true) {
     if (fixed_iters > 0) {
@@ -838,7 +1039,9 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       solve_apply<T, N>(
           C, G, t, X,
           [&](size_t g, int k, bool interior) {
-            const T zv = P ? fma(C.sw[k], T(__ldcg(P->uc + g / NN)), T(__ldcg(P->z + g))) : __ldcg(V.r + g);
+            const T zv = spec ? T(__ldcg(P->z + g))
+                         : P  ? fma(C.sw[k], T(__ldcg(P->uc + g / NN)), T(__ldcg(P->z + g)))
+                              : __ldcg(V.r + g);
             const T pv = first ? zv : fma(beta, __ldcg(pin + g), zv);
             if (interior) __stcg(pout + g, pv);
             return pv;
@@ -863,7 +1066,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
     const T alpha = rz / pqs;
     // Phase B: y += alpha p, r -= alpha q, r.r (and the cell part of the preconditioner).
     T rrb = T(0), rzb = T(0);
-    if (!P) {
+    if (!P || spec) {
       for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) {
         const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
         const T yv = fma(alpha, pv, __ldcg(V.y + i));
@@ -878,7 +1081,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
         const int nin = B.TYe * B.TXe * NN;
         for (int i = threadIdx.x; i < nin; i += blockDim.x) {
           const int c = i / NN, k = i - (i / NN) * NN;
-          const int ry = c / B.TXe, rx = c - (c / B.TXe) * B.TXe;
+          const int ry = quot(c, B.mTXe), rx = c - ry * B.TXe;
           const size_t g = ((size_t)(B.ty0 + ry) * G.Nx + (B.tx0 + rx)) * NN + k;
           const T pv = __ldcg(pout + g), qv = __ldcg(V.q + g);
           const T yv = fma(alpha, pv, __ldcg(V.y + g));
@@ -901,7 +1104,21 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
       return it;
     }
     T rznew = rnew;
-    if (P) {
+    if (fixed_iters == 0 && double(rnew) <= tol2 * double(rhob)) {
+      // converged by the recursive residual: the next pass verifies the true residual and, on
+      // a restart, preconditions that one, so this residual needs no preconditioning
+      rr = rnew;
+      cur ^= 1;
+      first = false;
+      ++it;
+      continue;
+    }
+    if (spec) {
+      if (!pc_spectral<TP, N, T>(G, *P, V.r, X, rznew)) {
+        flags |= kFlagTimeout;
+        return it;
+      }
+    } else if (P) {
       T ucrc = T(0);
       if (!pc_coarse<TP, T>(G, *P, X, ucrc)) {
         flags |= kFlagTimeout;
@@ -947,7 +1164,7 @@ struct CgArgs {
   double ca, cb;
   int x_unscaled;
   CgVectors<T> v;
-  int precond;          // 0: W^-1 (plain CG on the scaled system), 1: two-level
+  int precond;          // kPrecondJacobi (W^-1: plain CG on the scaled system), kPrecondTwoLevel or kPrecondSpectral
   PrecondArgs<TP> pc;   // (TP = float: the preconditioner applied in float32)
   double* psi_out;      // if non-null: psi = y / sqrt(W) at the end
   T* part;              // 6 * gridDim.x
@@ -974,12 +1191,22 @@ __host__ __device__ constexpr size_t cg_tile_values(int TY, int TX) {
   return (size_t)(TY + 2) * (TX + 2) * (N * N + 1 + 4 * N);
 }
 
+// Bytes of the DFT line buffers of a preconditioner (kind: PrecondArgs): two lines for the
+// two-level coarse solve, N lines (2N for a length that is not a power of two) for the spectral
+// one; pow2: both cell counts are powers of two.
 template <typename T, int N>
-__host__ __device__ constexpr size_t cg_smem_bytes(int TY, int TX, int Lmax, bool pc) {
-  return (pc ? align16(sizeof(T) * N * N * N * N) : 0) +
-         align16(cg_tile_values<T, N>(TY, TX) * sizeof(T) > (pc ? 2 * (size_t)Lmax * sizeof(Cplx<T>) : 0)
+__host__ __device__ constexpr size_t pc_line_bytes(int kind, int Lmax, bool pow2) {
+  return kind == kPrecondTwoLevel   ? 2 * (size_t)Lmax * sizeof(Cplx<T>)
+         : kind == kPrecondSpectral ? (pow2 ? 1 : 2) * (size_t)N * Lmax * sizeof(Cplx<T>)
+                                    : 0;
+}
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t cg_smem_bytes(int TY, int TX, int Lmax, int kind, bool pow2) {
+  return (kind == kPrecondTwoLevel ? align16(sizeof(T) * N * N * N * N) : 0) +
+         align16(cg_tile_values<T, N>(TY, TX) * sizeof(T) > pc_line_bytes<T, N>(kind, Lmax, pow2)
                      ? cg_tile_values<T, N>(TY, TX) * sizeof(T)
-                     : 2 * (size_t)Lmax * sizeof(Cplx<T>));
+                     : pc_line_bytes<T, N>(kind, Lmax, pow2));
 }
 
 // Lays out the solve context over dynamic shared memory starting at base (bytes).
@@ -1015,7 +1242,7 @@ template <typename T, int N, typename TP = T>
 __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, const CgArgs<T, TP>& A,
                                          SolveCtx<T>& X) {
   constexpr int NN = N * N;
-  const bool pc = A.precond == 1;
+  const bool pc = A.precond != kPrecondJacobi;
   X.sync = A.sync;
   X.part = A.part;
   X.phase = 0;
@@ -1136,7 +1363,7 @@ struct MixedArgs {
   double* psi_out;     // if non-null: psi = y / sqrt(W) at the end
   float* rf;           // float32 copy of the float64 residual (inner right-hand side)
   CgVectors<float> v;  // inner solve: y = e, r, p0, p1, q
-  int precond;         // 0: W^-1, 1: two-level (inner float32 solve)
+  int precond;         // kPrecondJacobi, kPrecondTwoLevel or kPrecondSpectral (inner float32 solve)
   PrecondArgs<float> pc;
   double* partd;       // 6 * gridDim.x
   float* partf;        // 6 * gridDim.x
@@ -1162,11 +1389,11 @@ __host__ __device__ constexpr size_t mixed_ops_bytes() {
 }
 
 template <int N>
-__host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX, int Lmax, bool pc) {
-  return (pc ? align16(sizeof(float) * N * N * N * N) : 0) +
-         align16(cg_tile_values<double, N>(TY, TX) * sizeof(double) > 2 * (size_t)Lmax * sizeof(Cplx<float>)
+__host__ __device__ constexpr size_t mixed_smem_bytes(int TY, int TX, int Lmax, int kind, bool pow2) {
+  return (kind == kPrecondTwoLevel ? align16(sizeof(float) * N * N * N * N) : 0) +
+         align16(cg_tile_values<double, N>(TY, TX) * sizeof(double) > pc_line_bytes<float, N>(kind, Lmax, pow2)
                      ? cg_tile_values<double, N>(TY, TX) * sizeof(double)
-                     : 2 * (size_t)Lmax * sizeof(Cplx<float>));
+                     : pc_line_bytes<float, N>(kind, Lmax, pow2));
 }
 
 // One float64 residual pass: r = b - Ahat y (y staged with halo; pass 0: y = y0), rf =
@@ -1209,7 +1436,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
                                             const OpsK<df, N>& Ck, const Geom& G, const MixedArgs& A,
                                             SolveCtx<float>& Xf, SolveCtx<double>& Xd) {
   constexpr int NN = N * N;
-  const bool pc = A.precond == 1;
+  const bool pc = A.precond != kPrecondJacobi;
   // the double-float apply stages its tiles in the float64 buffers
   Xf.wU = reinterpret_cast<df*>(Xd.sU);
   Xf.wXR = reinterpret_cast<df*>(Xd.tXR);
@@ -1335,7 +1562,7 @@ __global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_cons
   __shared__ float redf[32];
   __shared__ float bcf;
   __shared__ int s_flag;
-  const bool pc = A.precond == 1;
+  const bool pc = A.precond == kPrecondTwoLevel;  // the cell blocks are staged
   const int Lmax = max(G.Nx, G.Ny);
   const Ops2D<double, N>& Cds = stage_table(Cd, smem_raw);
   const Ops2D<float, N>& Cfs = stage_table(Cf, smem_raw + table_bytes<Ops2D<double, N>>());
@@ -1467,7 +1694,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
       stage_table(*static_cast<const Ops2D<float, N>*>(S.ops_f), smem_all + table_bytes<Ops2D<double, N>>());
   const OpsK<df, N>& Ck = stage_table(*static_cast<const OpsK<df, N>*>(S.ops_k),
                                       smem_all + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>());
-  const bool pc = S.precond == 1;
+  const bool pc = S.precond == kPrecondTwoLevel;  // the cell blocks are staged
   const int Lmax = max(S.Gc.Nx, S.Gc.Ny);
   if (S.precision == 0) {
     CgArgs<double> A{};

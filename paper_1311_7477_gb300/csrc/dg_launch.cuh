@@ -65,7 +65,7 @@ template <typename T, int N, typename TP>
 int launch_cg(const dg_grid* g, CgArgs<T, TP> A, const Workspace& w, cudaStream_t st, dg_sim* timed) {
   bool cluster = false;
   Geom G = solve_geom(g, false, &cluster);
-  size_t smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+  size_t smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond, pow2_grid(g));
   auto kern = cg_kernel<T, N, TP>;
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
@@ -89,7 +89,7 @@ int launch_cg(const dg_grid* g, CgArgs<T, TP> A, const Workspace& w, cudaStream_
   if (int rc = launch_solve(kern, cluster, grid, smem, st, &launched, ops_of<T, N>(g), G, A)) return rc;
   if (!launched) {  // no room for the cluster: the tiles of a cooperative launch instead
     G = geom_of(g, g->cTY, g->cTX);
-    smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+    smem = table_bytes<Ops2D<T, N>>() + cg_smem_bytes<T, N>(G.TY, G.TX, std::max(g->Nx, g->Ny), A.precond, pow2_grid(g));
     if (int rc = set_smem(kern, smem)) return rc;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     grid = std::min({per_sm * g->num_sms, G.tilesX * G.tilesY, w.grid_cap});
@@ -106,7 +106,7 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
   bool cluster = false;
   Geom G = solve_geom(g, true, &cluster);
   auto smem_of = [&](const Geom& Gx) {
-    return mixed_ops_bytes<N>() + mixed_smem_bytes<N>(Gx.TY, Gx.TX, std::max(g->Nx, g->Ny), A.precond == 1);
+    return mixed_ops_bytes<N>() + mixed_smem_bytes<N>(Gx.TY, Gx.TX, std::max(g->Nx, g->Ny), A.precond, pow2_grid(g));
   };
   size_t smem = smem_of(G);
   auto kern = mixed_cg_kernel<N>;

@@ -3,7 +3,9 @@
 // Sec. 6: the LDG Laplacian with alternating fluxes and jump penalty tau).
 #include "dg_tables.h"
 
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 namespace dgk {
@@ -141,6 +143,79 @@ int build_ref_tables(int n, double tau, RefTables* t) {
     double s = 0.0;
     for (int k = 0; k < n; ++k) s += G0d[k][i] * wh[k] * liftR[k];
     t->betaFirst[i] = s;
+  }
+  return 0;
+}
+
+int hermitian_eig(int m, const long double* Hre, const long double* Him, double* lam, double* Vre, double* Vim) {
+  using R = long double;
+  using cd = std::complex<R>;
+  cd H[kMaxN][kMaxN], V[kMaxN][kMaxN];
+  R fro = 0.0L;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      H[i][j] = cd(Hre[i * m + j], Him[i * m + j]);
+      V[i][j] = cd(i == j ? 1.0L : 0.0L, 0.0L);
+      fro += std::norm(H[i][j]);
+    }
+  fro = std::sqrt(fro);
+  bool done = m < 2 || fro == 0.0L;
+  for (int sweep = 0; sweep < 60 && !done; ++sweep) {
+    R off = 0.0L;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        if (i != j) off += std::norm(H[i][j]);
+    if (std::sqrt(off) <= 1e-18L * fro) {
+      done = true;
+      break;
+    }
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const R beta = std::abs(H[p][q]);
+        if (beta == 0.0L) continue;
+        // U = D R: D_qq = e^{-i phi} makes the (p, q) entry real (|h_pq|), R the plane rotation
+        // with R_pp = R_qq = c, R_pq = s, R_qp = -s that zeroes it.
+        const cd e = std::conj(H[p][q]) / beta;  // e^{-i phi}
+        const R alpha = H[p][p].real(), gamma = H[q][q].real();
+        const R tau = (gamma - alpha) / (2.0L * beta);
+        const R t = (tau >= 0.0L ? 1.0L : -1.0L) / (std::fabs(tau) + std::sqrt(1.0L + tau * tau));
+        const R c = 1.0L / std::sqrt(1.0L + t * t), s = t * c;
+        const cd Upp = c, Upq = s, Uqp = -s * e, Uqq = c * e;
+        // H <- U^* H U (columns p, q, then rows p, q), V <- V U
+        for (int i = 0; i < m; ++i) {
+          const cd hp = H[i][p], hq = H[i][q];
+          H[i][p] = hp * Upp + hq * Uqp;
+          H[i][q] = hp * Upq + hq * Uqq;
+          const cd vp = V[i][p], vq = V[i][q];
+          V[i][p] = vp * Upp + vq * Uqp;
+          V[i][q] = vp * Upq + vq * Uqq;
+        }
+        for (int j = 0; j < m; ++j) {
+          const cd hp = H[p][j], hq = H[q][j];
+          H[p][j] = std::conj(Upp) * hp + std::conj(Uqp) * hq;
+          H[q][j] = std::conj(Upq) * hp + std::conj(Uqq) * hq;
+        }
+        H[p][q] = H[q][p] = 0.0L;
+        H[p][p] = H[p][p].real();
+        H[q][q] = H[q][q].real();
+      }
+  }
+  if (!done) {
+    R off = 0.0L;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        if (i != j) off += std::norm(H[i][j]);
+    if (std::sqrt(off) > 1e-15L * fro) return -1;
+  }
+  int order[kMaxN];
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::sort(order, order + m, [&](int x, int y) { return H[x][x].real() < H[y][y].real(); });
+  for (int j = 0; j < m; ++j) {
+    lam[j] = double(H[order[j]][order[j]].real());
+    for (int i = 0; i < m; ++i) {
+      Vre[i * m + j] = double(V[i][order[j]].real());
+      Vim[i * m + j] = double(V[i][order[j]].imag());
+    }
   }
   return 0;
 }

@@ -35,4 +35,13 @@ constexpr double kDirichletPenalty = 1.0;  // (penalty / h) u(a)^2 on the left b
 // Fills t for 1 <= n <= kMaxN and penalty tau >= 0.  Returns 0 on success.
 int build_ref_tables(int n, double tau, RefTables* t);
 
+// Eigen-decomposition of a Hermitian m x m matrix (m <= kMaxN) given row-major by its real and
+// imaginary parts: H = V diag(lam) V^*, V unitary (column j = eigenvector j), lam ascending.
+// Cyclic Jacobi rotations, each of which zeroes one off-diagonal pair (a phase that makes the
+// pair real, then a real plane rotation), in long double: the small eigenvalues of the
+// operators' symbols (about 1 against 1e7 and more) then come out accurate to float64
+// precision.  Returns 0, or -1 when the off-diagonal part is not below 1e-15 of the matrix's
+// Frobenius norm after 60 sweeps.
+int hermitian_eig(int m, const long double* Hre, const long double* Him, double* lam, double* Vre, double* Vim);
+
 }  // namespace dgk

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libdgk.so")
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_NOMEM, DG_ERR_NOCONV, DG_ERR_NONFINITE, DG_ERR_TIMEOUT, DG_ERR_IO = range(8)
 DG_FP64, DG_MIXED, DG_MIXED64, DG_FP64_PC32 = 0, 1, 2, 3
 DG_BC_PERIODIC, DG_BC_DIRICHLET = 0, 1
-DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL = 0, 1
+DG_PRECOND_JACOBI, DG_PRECOND_TWOLEVEL, DG_PRECOND_SPECTRAL = 0, 1, 2
 DG_BRACKET_ARAKAWA, DG_BRACKET_NAIVE = 0, 1
 
 ERROR_NAMES = {DG_ERR_ARG: "DG_ERR_ARG", DG_ERR_CUDA: "DG_ERR_CUDA", DG_ERR_NOMEM: "DG_ERR_NOMEM",
@@ -53,6 +53,7 @@ def _load():
         "dg_selftest_wait_cap": (I, [P]),
         "dg_ref_tables_len": (I, [I]),
         "dg_ref_tables": (I, [I, D, PD, I]),
+        "dg_spectral_symbol": (I, [I, I, D, D, I, PD, PD, PD]),
         "dg_grid_create": (I, [PP, I, I, I, D, D, D]),
         "dg_grid_create_bc": (I, [PP, I, I, I, D, D, D, I]),
         "dg_grid_destroy": (I, [P]),
@@ -176,6 +177,19 @@ def ref_tables(n, tau=0.0):
     return res
 
 
+def spectral_symbol(N, n, L, k, tau=0.0):
+    """Host-only (dg_spectral_symbol): eigenvalues lam (ascending) and unitary eigenvectors V
+    (columns) of the scaled 1D CG operator's symbol at wave number k of a periodic line of N
+    cells of length L."""
+    import numpy as np
+    lam = (ctypes.c_double * n)()
+    vre = (ctypes.c_double * (n * n))()
+    vim = (ctypes.c_double * (n * n))()
+    _check(_lib.dg_spectral_symbol(int(N), int(n), float(L), float(tau), int(k), lam, vre, vim))
+    V = (np.frombuffer(vre, dtype=np.float64) + 1j * np.frombuffer(vim, dtype=np.float64)).reshape(n, n)
+    return np.frombuffer(lam, dtype=np.float64).copy(), V
+
+
 class Grid:
     """dg_grid: [0, Lx] x [0, Ly], Nx x Ny cells, n nodes per cell and dimension; periodic
     (bc="periodic") or homogeneous Dirichlet (bc="dirichlet") boundaries."""
@@ -211,9 +225,10 @@ class Grid:
         _check(_lib.dg_grid_set_tiles(self.h, int(TY), int(TX)))
 
     def set_precond(self, kind):
-        """DG_PRECOND_JACOBI (W^-1) or DG_PRECOND_TWOLEVEL; also accepts "jacobi" / "twolevel"."""
+        """DG_PRECOND_JACOBI (W^-1), DG_PRECOND_TWOLEVEL or DG_PRECOND_SPECTRAL; also accepts
+        "jacobi" / "twolevel" / "spectral"."""
         if isinstance(kind, str):
-            kind = {"jacobi": DG_PRECOND_JACOBI, "twolevel": DG_PRECOND_TWOLEVEL}[kind]
+            kind = {"jacobi": DG_PRECOND_JACOBI, "twolevel": DG_PRECOND_TWOLEVEL, "spectral": DG_PRECOND_SPECTRAL}[kind]
         _check(_lib.dg_grid_set_precond(self.h, int(kind)))
 
     def set_compensated_apply(self, mode):

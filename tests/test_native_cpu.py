@@ -77,3 +77,31 @@ def test_no_device_fails_loudly(native):
     assert rc == native.DG_ERR_CUDA
     with pytest.raises(native.DGError):
         native.Grid(4, 4, 3)
+
+
+@pytest.mark.parametrize("n", range(1, 6))
+@pytest.mark.parametrize("N,k,tau", [(8, 0, 0.0), (8, 3, 0.0), (7, 2, 0.0), (1, 0, 0.0), (2, 1, 0.0),
+                                     (16, 8, 0.4), (1024, 1, 0.0), (1024, 512, 0.0)])
+def test_spectral_symbol_matches_oracle(native, n, N, k, tau):
+    """dg_spectral_symbol (the tables of the spectral preconditioner) against the oracle's LDG
+    stiffness: the symbol of the line scaled by w^-1/2 on both sides, built from the blocks of
+    the dense 1D matrix on three cells; eigenvalues, V diag(lam) V^* = K and V unitary."""
+    L = 2.0
+    lam, V = native.spectral_symbol(N, n, L, k, tau)
+    o = Tables(n)
+    h = L / N
+    A3 = ldg_matrix_1d(o, 3, h, tau)[n:2 * n, :]
+    w = h * o.w / 2.0
+    th = 2.0 * np.pi * k / N
+    K = (A3[:, n:2 * n] + np.exp(1j * th) * A3[:, 2 * n:] + np.exp(-1j * th) * A3[:, :n]) / np.sqrt(np.outer(w, w))
+    ev = np.linalg.eigvalsh(K)
+    if k == 0:
+        assert abs(ev[0]) <= 1e-9 * max(abs(ev[-1]), 1e-300)
+        ev[0] = 0.0
+        assert lam[0] == 0.0
+    # the symbol is a cancelling sum of the blocks: rounding is relative to their size
+    sc = max(np.abs(A3).max() / w.min(), 1e-300)
+    assert np.all(np.diff(lam) >= 0.0)
+    assert np.abs(lam - ev).max() <= 1e-13 * sc
+    assert np.abs(V @ np.diag(lam) @ V.conj().T - K).max() <= 1e-13 * sc
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() <= 1e-13
