@@ -358,7 +358,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed64", "fp64pc32"],
                     help="default: fp64 for the single runs, mixed for batch64 and serve")
-    ap.add_argument("--precond", default="twolevel", choices=["jacobi", "twolevel", "spectral"])
+    ap.add_argument("--precond", default="spectral", choices=["jacobi", "twolevel", "spectral"])
     ap.add_argument("--no-mixed-compare", action="store_true")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

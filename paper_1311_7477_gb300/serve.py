@@ -27,9 +27,10 @@ import numpy as np
 from . import dg, workloads
 
 # device bytes per dof of one simulation (state rings, RK stages, solver and preconditioner
-# vectors, grid workspace), float64 / mixed
-BYTES_PER_DOF = {dg.DG_FP64: 8 * 23, dg.DG_MIXED: 8 * 23 + 4 * 10, dg.DG_MIXED64: 8 * 23 + 4 * 10,
-                 dg.DG_FP64_PC32: 8 * 23 + 4 * 2}
+# vectors including the spectral preconditioner's half spectrum, grid workspace), float64 /
+# mixed
+BYTES_PER_DOF = {dg.DG_FP64: 8 * 24, dg.DG_MIXED: 8 * 24 + 4 * 11, dg.DG_MIXED64: 8 * 24 + 4 * 11,
+                 dg.DG_FP64_PC32: 8 * 24 + 4 * 3}
 
 
 def footprint(N, n, precision):
@@ -58,7 +59,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, max_active=64, hbm_budget=200e9, precision=dg.DG_MIXED, precond="twolevel", cg_tol=1e-10,
+    def __init__(self, max_active=64, hbm_budget=200e9, precision=dg.DG_MIXED, precond="spectral", cg_tol=1e-10,
                  chunk=8, dt_cap=2e-4, keep_results=False, groups=0):
         self.batch = dg.Batch(max_active)
         if groups:
