@@ -68,18 +68,19 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def measured_traffic(kernel, workload, precision, iters_per_launch=None):
-    """DRAM bytes (read + write) per launch of `kernel` on this workload and precision from the
-    ncu capture recorded in profiles/<kernel>_traffic.json, scaled from the capture's CG
-    iterations per launch to iters_per_launch (the traffic of a solve grows with its iteration
-    count; None if there is no record)."""
+def measured_traffic(kernel, workload, precision, iters_per_launch=None, precond=None):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload, precision and
+    preconditioner from the ncu capture recorded in profiles/<kernel>_traffic.json, scaled from
+    the capture's CG iterations per launch to iters_per_launch (the traffic of a solve grows
+    with its iteration count; None if there is no record)."""
     path = os.path.join(ROOT, "profiles", "%s_traffic.json" % kernel)
     try:
         rows = json.load(open(path))["captures"]
     except (OSError, KeyError, ValueError):
         return None
     for r in rows:
-        if r.get("workload") == workload and r.get("precision") == precision:
+        if (r.get("workload") == workload and r.get("precision") == precision
+                and (precond is None or r.get("precond") == precond)):
             b = float(r["dram_bytes_per_launch"])
             k = r.get("iters_per_launch")
             if iters_per_launch and k:
@@ -364,7 +365,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-steps-scale", type=float, default=0.02)
+    ap.add_argument("--serve-steps-scale", type=float, default=0.25)
     ap.add_argument("--serve-max-cells", type=int, default=1024)
     ap.add_argument("--serve-groups", type=int, default=0, help="block groups of the batch (0: automatic)")
     ap.add_argument("--batch-compare-fp64", action="store_true",
@@ -479,8 +480,7 @@ def main():
         ref.get(ref_w, ref_p)
         ref.close()
         what = {"fp64": "float64 throughout (the headline path)",
-                "fp64pc32": "float64 throughout except the CG preconditioner (cell block solve and coarse DFT "
-                            "solve), applied in float32",
+                "fp64pc32": "float64 throughout except the CG preconditioner, applied in float32",
                 "mixed64": "float64 bracket/viscous term/update, float32 inner PCG, float64 refinement residual",
                 "mixed": "bracket and viscous term in double-float on the float32 pipe, float32 inner PCG, "
                          "float64 update and refinement residual"}
@@ -527,7 +527,8 @@ def main():
                 entry["roofline"] = {"kernel": "mixed_cg_kernel", "bound": "hbm", "achieved": gbs,
                                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                                      "peak_source": peak_src,
-                                     "traffic": measured_traffic("cg_kernel", args.workload, mname),
+                                     "traffic": measured_traffic("cg_kernel", args.workload, mname,
+                                                                 precond=args.precond),
                                      "bytes_per_dof": "16 + 32 (sweeps + 1) + 32 x inner iterations"}
             modes[mname] = entry
             ms_.close()
@@ -572,7 +573,7 @@ def main():
     ach_m = dof * (flops_iter_m * it_per_launch + flops_setup_m) / sec / 1e12
     ach_i = dof * (flops_iter_i * it_per_launch + flops_setup_i) / sec / 1e12
     gbs_m = dof * (bytes_iter_m * it_per_launch + bytes_setup_m) / sec / 1e9
-    traffic = measured_traffic("cg_kernel", args.workload, args.precision, it_per_launch)
+    traffic = measured_traffic("cg_kernel", args.workload, args.precision, it_per_launch, args.precond)
     roof = {"kernel": "cg_kernel (persistent CG Poisson solve)", "bound": "alu",
             "achieved": ach_m, "peak": pk, "unit": "TFLOP/s", "frac": ach_m / pk, "traffic": traffic,
             "peak_source": ("FP64" if fp64 else "FP32") + " FMA pipe, " + fma_src,

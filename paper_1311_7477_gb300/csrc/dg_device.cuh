@@ -276,6 +276,30 @@ __device__ __forceinline__ void dirichlet_ghost_traces(const Geom& G, const Tile
   }
 }
 
+// ---- grid-stride passes --------------------------------------------------------------------
+
+// A grid-stride loop over [first, n) in rounds of U strides: the loads of a round (ld(i)) are
+// all issued before its uses (use(i, value), in increasing i, so sums accumulate in the same
+// order as a plain loop).  With one load in flight per thread, the 16-32 resident warps of an
+// SM reach a fraction of the HBM bandwidth; U loads in flight multiply it.
+template <int U, class Ld, class Use>
+__device__ __forceinline__ void strided_pass(size_t first, size_t n, size_t stride, Ld&& ld, Use&& use) {
+  using V = decltype(ld(size_t(0)));
+  for (size_t i0 = first; i0 < n; i0 += U * stride) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i < n) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i < n) use(i, v[u]);
+    }
+  }
+}
+
 // ---- reductions ------------------------------------------------------------------------
 
 template <typename T>
@@ -528,6 +552,22 @@ __device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, i
       half = 2;
       lh = 1;
     }
+    if (half == 1 && L >= 4) {  // the first pass: every twiddle is 1
+      for (int t = tid; t < count * q; t += nth) {
+        Cplx<T>* b = s + (t >> (log2L - 2)) * L + 4 * (t & (q - 1));
+        const Cplx<T> a = b[0], bb = b[1], c = b[2], d = b[3];
+        const Cplx<T> A1 = cadd(a, bb), B1 = csub(a, bb), C1 = cadd(c, d);
+        Cplx<T> D1 = csub(c, d);
+        D1 = inverse ? Cplx<T>{-D1.im, D1.re} : Cplx<T>{D1.im, -D1.re};
+        b[0] = cadd(A1, C1);
+        b[2] = csub(A1, C1);
+        b[1] = cadd(B1, D1);
+        b[3] = csub(B1, D1);
+      }
+      __syncthreads();
+      half = 4;
+      lh = 2;
+    }
     for (; half < L; half <<= 2, lh += 2) {
       const int s2 = L / (2 * half), s4 = L / (4 * half);
       for (int t = tid; t < count * q; t += nth) {
@@ -556,6 +596,21 @@ __device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, i
     // spans 2h and h per pass, from 2h = L / 2 down; a last span-1 stage if log2L is odd
     int h = q, lh = log2L - 2, stages = log2L;
     for (; stages >= 2; h >>= 2, lh -= 2, stages -= 2) {
+      if (h == 1) {  // the last pass: every twiddle is 1
+        for (int t = tid; t < count * q; t += nth) {
+          Cplx<T>* b = s + (t >> (log2L - 2)) * L + 4 * (t & (q - 1));
+          const Cplx<T> x0 = b[0], x1 = b[1], x2 = b[2], x3 = b[3];
+          const Cplx<T> y0 = cadd(x0, x2), y1 = cadd(x1, x3), y2 = csub(x0, x2);
+          Cplx<T> y3 = csub(x1, x3);
+          y3 = inverse ? Cplx<T>{-y3.im, y3.re} : Cplx<T>{y3.im, -y3.re};
+          b[0] = cadd(y0, y1);
+          b[1] = csub(y0, y1);
+          b[2] = cadd(y2, y3);
+          b[3] = csub(y2, y3);
+        }
+        __syncthreads();
+        continue;
+      }
       const int s4 = L / (4 * h), s2 = L / (2 * h);
       for (int t = tid; t < count * q; t += nth) {
         const int line = t >> (log2L - 2), tt = t & (q - 1);

@@ -655,6 +655,12 @@ __device__ __forceinline__ Cplx<T> ld_cplx(const Cplx<T>* p) {
   return Cplx<T>{__ldcg(&p->re), __ldcg(&p->im)};
 }
 
+// read-only tables (L1-cached)
+template <typename T>
+__device__ __forceinline__ Cplx<T> ld_cplx_ro(const Cplx<T>* p) {
+  return Cplx<T>{__ldg(&p->re), __ldg(&p->im)};
+}
+
 template <typename T>
 __device__ __forceinline__ void st_cplx(Cplx<T>* p, Cplx<T> v) {
   __stcg(&p->re, v.re);
@@ -788,7 +794,7 @@ __device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondAr
         Cplx<TP> ta{TP(0), TP(0)}, tb{TP(0), TP(0)};
 #pragma unroll
         for (int b = 0; b < N; ++b) {
-          const Cplx<TP> v = V[b * N + j];  // conj(v) * x
+          const Cplx<TP> v = ld_cplx_ro(V + b * N + j);  // conj(v) * x
           ta.re = fma(v.re, A[b].re, fma(v.im, A[b].im, ta.re));
           ta.im = fma(v.re, A[b].im, fma(-v.im, A[b].re, ta.im));
           tb.re = fma(v.re, B[b].re, fma(v.im, B[b].im, tb.re));
@@ -822,17 +828,17 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
     const TP lxj = P.lx[kx * N + j];
     for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
       const Cplx<TP>* V = P.Vy + (size_t)ky * N * N;
-      Cplx<TP> x[N], t[N];
-#pragma unroll
-      for (int a = 0; a < N; ++a) x[a] = L0[a * Ny + ky];
+      // the n x n transform is read row by row from L1 in both directions (holding all of V
+      // in registers for both would spill)
+      Cplx<TP> t[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         Cplx<TP> acc{TP(0), TP(0)};
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          const Cplx<TP> v = V[a * N + i];
-          acc.re = fma(v.re, x[a].re, fma(v.im, x[a].im, acc.re));
-          acc.im = fma(v.re, x[a].im, fma(-v.im, x[a].re, acc.im));
+          const Cplx<TP> v = ld_cplx_ro(V + a * N + i), x = L0[a * Ny + ky];
+          acc.re = fma(v.re, x.re, fma(v.im, x.im, acc.re));
+          acc.im = fma(v.re, x.im, fma(-v.im, x.re, acc.im));
         }
         const TP den = P.ly[ky * N + i] + lxj;
         const TP f = den == TP(0) ? TP(0) : scale / den;
@@ -842,7 +848,7 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
       for (int a = 0; a < N; ++a) {
         Cplx<TP> acc{TP(0), TP(0)};
 #pragma unroll
-        for (int i = 0; i < N; ++i) acc = cadd(acc, cmul(V[a * N + i], t[i]));
+        for (int i = 0; i < N; ++i) acc = cadd(acc, cmul(ld_cplx_ro(V + a * N + i), t[i]));
         L0[a * Ny + ky] = acc;
       }
     }
@@ -886,7 +892,7 @@ __device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondAr
         Cplx<TP> A{TP(0), TP(0)}, B{TP(0), TP(0)};
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const Cplx<TP> v = V[b * N + j];
+          const Cplx<TP> v = ld_cplx_ro(V + b * N + j);
           A = cadd(A, cmul(v, ta[j]));
           B = cadd(B, cmul(v, tb[j]));
         }
@@ -1067,14 +1073,19 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
     // Phase B: y += alpha p, r -= alpha q, r.r (and the cell part of the preconditioner).
     T rrb = T(0), rzb = T(0);
     if (!P || spec) {
-      for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride) {
-        const T pv = __ldcg(pout + i), qv = __ldcg(V.q + i);
-        const T yv = fma(alpha, pv, __ldcg(V.y + i));
-        const T rv = fma(-alpha, qv, __ldcg(V.r + i));
-        __stcg(V.y + i, yv);
-        __stcg(V.r + i, rv);
-        rrb = fma(rv, rv, rrb);
-      }
+      struct Pqyr {
+        T p, q, y, r;
+      };
+      strided_pass<2>(
+          (size_t)X.vrank * blockDim.x + threadIdx.x, ndof, stride,
+          [&](size_t i) { return Pqyr{__ldcg(pout + i), __ldcg(V.q + i), __ldcg(V.y + i), __ldcg(V.r + i)}; },
+          [&](size_t i, const Pqyr& v) {
+            const T yv = fma(alpha, v.p, v.y);
+            const T rv = fma(-alpha, v.q, v.r);
+            __stcg(V.y + i, yv);
+            __stcg(V.r + i, rv);
+            rrb = fma(rv, rv, rrb);
+          });
     } else {
       for (int t = X.vrank; t < ntiles; t += X.vsize) {
         const TileBox B = make_box(G, t);
@@ -1144,14 +1155,15 @@ __device__ __forceinline__ bool project_mean(const Ops2D<T, N>& C, const Geom& G
   constexpr int NN = N * N;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)X.vsize * blockDim.x;
+  const size_t first = (size_t)X.vrank * blockDim.x + threadIdx.x;
   T s = T(0);
-  for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-    s = fma(C.sw[i % NN], __ldcg(y + i), s);
+  strided_pass<4>(first, ndof, stride, [&](size_t i) { return __ldcg(y + i); },
+                  [&](size_t i, T v) { s = fma(C.sw[i % NN], v, s); });
   T m = T(0);
   if (!reduce_all(X, s, m)) return false;
   m = m / T(sumW);
-  for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-    __stcg(y + i, fma(-m, C.sw[i % NN], __ldcg(y + i)));
+  strided_pass<4>(first, ndof, stride, [&](size_t i) { return __ldcg(y + i); },
+                  [&](size_t i, T v) { __stcg(y + i, fma(-m, C.sw[i % NN], v)); });
   return solve_barrier(X);
 }
 
@@ -1258,8 +1270,9 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
   if (A.rhs == nullptr && !A.keep_mean) {
     for (int pass = 0; pass < 2; ++pass) {
       T s = T(0);
-      for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-        s = fma(C.wq[i % NN], T(A.omega[i]) - wbar, s);
+      strided_pass<4>((size_t)X.vrank * blockDim.x + threadIdx.x, ndof, stride,
+                      [&](size_t i) { return T(A.omega[i]); },
+                      [&](size_t i, T v) { s = fma(C.wq[i % NN], v - wbar, s); });
       T m = T(0);
       if (!reduce_all(X, s, m)) {
         flags |= kFlagTimeout;
@@ -1309,8 +1322,9 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
   }
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
-    for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-      A.psi_out[i] = double(__ldcg(A.v.y + i) * C.isw[i % NN]);
+    strided_pass<4>((size_t)X.vrank * blockDim.x + threadIdx.x, ndof, stride,
+                    [&](size_t i) { return __ldcg(A.v.y + i); },
+                    [&](size_t i, T v) { A.psi_out[i] = double(v * C.isw[i % NN]); });
   }
   if (X.vrank == 0 && threadIdx.x == 0) {
     SolveStatus* st = A.status;
@@ -1326,8 +1340,12 @@ finish:
   }
 }
 
-template <typename T, int N, typename TP = T>
-__global__ void __launch_bounds__(kThreads, N == 5 ? 4 : 3) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
+// MinB: the blocks per SM the register budget is sized for.  The solves with the spectral
+// preconditioner are launched with MinB = 2 (up to 128 registers a thread: its V transforms
+// keep n complex values per row in registers, and its line buffers allow two blocks per SM on
+// large grids anyway).
+template <typename T, int N, typename TP = T, int MinB = (N == 5 ? 4 : 3)>
+__global__ void __launch_bounds__(kThreads, MinB) cg_kernel(const __grid_constant__ Ops2D<T, N> C, const Geom G,
                                                         const __grid_constant__ CgArgs<T, TP> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[32];
@@ -1457,8 +1475,9 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   double rr = 0.0, bb = 0.0, wbar = 0.0, rr_prev = -1.0;
   for (int mp = 0; mp < (A.keep_mean ? 0 : 2); ++mp) {  // two-pass W-mean, as in cg_kernel
     double s = 0.0;
-    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-      s = fma(Cd.wq[i % NN], A.omega[i] - wbar, s);
+    strided_pass<4>((size_t)Xd.vrank * blockDim.x + threadIdx.x, ndof, stride,
+                    [&](size_t i) { return A.omega[i]; },
+                    [&](size_t i, double v) { s = fma(Cd.wq[i % NN], v - wbar, s); });
     double m = 0.0;
     if (!reduce_all(Xd, s, m)) {
       flags |= kFlagTimeout;
@@ -1521,8 +1540,13 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
       goto finish;
     }
     // y += e
-    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-      __stcg(A.y + i, __ldcg(A.y + i) + double(__ldcg(A.v.y + i)));
+    struct Ye {
+      double y;
+      float e;
+    };
+    strided_pass<4>((size_t)Xd.vrank * blockDim.x + threadIdx.x, ndof, stride,
+                    [&](size_t i) { return Ye{__ldcg(A.y + i), __ldcg(A.v.y + i)}; },
+                    [&](size_t i, const Ye& v) { __stcg(A.y + i, v.y + double(v.e)); });
     if (!solve_barrier(Xd)) {
       flags |= kFlagTimeout;
       goto finish;
@@ -1532,8 +1556,9 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   if (pc && !(flags & kFlagTimeout) && !project_mean<double, N>(Cd, G, A.y, A.sumW, Xd)) flags |= kFlagTimeout;
 finish:
   if (A.psi_out && !(flags & kFlagTimeout)) {
-    for (size_t i = (size_t)Xd.vrank * blockDim.x + threadIdx.x; i < ndof; i += stride)
-      A.psi_out[i] = __ldcg(A.y + i) * Cd.isw[i % NN];
+    strided_pass<4>((size_t)Xd.vrank * blockDim.x + threadIdx.x, ndof, stride,
+                    [&](size_t i) { return __ldcg(A.y + i); },
+                    [&](size_t i, double v) { A.psi_out[i] = v * Cd.isw[i % NN]; });
   }
   if (Xd.vrank == 0 && threadIdx.x == 0) {
     SolveStatus* st = A.status;
@@ -1550,8 +1575,8 @@ finish:
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 4) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
+template <int N, int MinB = 4>
+__global__ void __launch_bounds__(kThreads, MinB) mixed_cg_kernel(const __grid_constant__ Ops2D<double, N> Cd,
                                                            const __grid_constant__ Ops2D<float, N> Cf,
                                                            const __grid_constant__ OpsK<df, N> Ck, const Geom G,
                                                            const __grid_constant__ MixedArgs A) {

@@ -70,6 +70,13 @@ int launch_cg(const dg_grid* g, CgArgs<T, TP> A, const Workspace& w, cudaStream_
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  if (A.precond == kPrecondSpectral && per_sm <= 2) {
+    // the spectral line buffers leave room for two blocks per SM: the variant whose register
+    // budget assumes two (no spills in the spectral transforms)
+    kern = cg_kernel<T, N, TP, 2>;
+    if (int rc = set_smem(kern, smem)) return rc;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  }
   if (per_sm < 1) return fail(DG_ERR_CUDA, "CG kernel does not fit on an SM (smem %zu B)", smem);
   int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
   grid = std::min(grid, w.grid_cap);
@@ -113,6 +120,11 @@ int launch_mixed(const dg_grid* g, MixedArgs A, const Workspace& w, cudaStream_t
   if (int rc = set_smem(kern, smem)) return rc;
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  if (A.precond == kPrecondSpectral && per_sm <= 2) {  // as in launch_cg
+    kern = mixed_cg_kernel<N, 2>;
+    if (int rc = set_smem(kern, smem)) return rc;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  }
   if (per_sm < 1) return fail(DG_ERR_CUDA, "mixed CG kernel does not fit on an SM (smem %zu B)", smem);
   int grid = std::min(per_sm * g->num_sms, G.tilesX * G.tilesY);
   grid = std::min(grid, w.grid_cap);
