@@ -362,7 +362,7 @@ struct SyncState {
   unsigned int count;
   unsigned int gen;
   int error;
-  int pad;
+  unsigned int ticket;  // work-unit tickets of the dynamically scheduled phases (next_unit)
 };
 
 // Waits of a block at the barrier give up after this many polls (~1 s with the sleep

@@ -405,6 +405,7 @@ struct SolveCtx {
   SyncState* sync;
   T* part;                        // 6 * vsize: two alternating halves of up to 3 sums
   int phase;
+  unsigned int tbase;             // first ticket of the next dynamically scheduled phase
   int vrank, vsize;               // this block's rank and the block count of the (virtual) grid
   int cluster;                    // the whole grid is one thread-block cluster
   // float32 solves: if kdf is set (an OpsK<df, N> in shared memory), the operator Ahat is
@@ -423,6 +424,31 @@ __device__ __forceinline__ bool solve_barrier(SolveCtx<T>& X) {
     return true;
   }
   return grid_barrier(X.sync, X.s_flag, X.vsize);
+}
+
+// Dynamic distribution of a phase's work units over the blocks of a solve: each block takes
+// the next unit from the ticket counter of the solve's SyncState until the units run out.
+// Every block draws exactly one ticket past the last unit, so a phase consumes units + vsize
+// tickets and every block knows where the next phase's tickets start (X.tbase, read from
+// the counter by every block at the start of the solve, before its first barrier).  Units
+// write disjoint outputs, so the results do not depend on which block takes which unit.
+template <typename T>
+__device__ __forceinline__ int next_unit(SolveCtx<T>& X, int units) {
+  int* s = reinterpret_cast<int*>(X.red);
+  __syncthreads();  // every thread has read the previous unit number
+  if (threadIdx.x == 0) s[0] = int(atomicAdd(&X.sync->ticket, 1u) - X.tbase);
+  __syncthreads();
+  return s[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void end_units(SolveCtx<T>& X, int units) {
+  X.tbase += unsigned(units) + unsigned(X.vsize);
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned int read_ticket(const SyncState* s) {
+  return *reinterpret_cast<const volatile unsigned int*>(&s->ticket);
 }
 
 // Block partials of one or two sums -> grid barrier -> the sums in every block (fixed order).
@@ -655,10 +681,15 @@ __device__ __forceinline__ Cplx<T> ld_cplx(const Cplx<T>* p) {
   return Cplx<T>{__ldcg(&p->re), __ldcg(&p->im)};
 }
 
-// read-only tables (L1-cached)
+// An entry of the spectral preconditioner's n x n transforms.  In float64 through the
+// read-only path (the compiler then keeps them out of registers: holding a whole float64
+// transform per direction would spill); in float32 a plain load (measured faster).
 template <typename T>
-__device__ __forceinline__ Cplx<T> ld_cplx_ro(const Cplx<T>* p) {
-  return Cplx<T>{__ldg(&p->re), __ldg(&p->im)};
+__device__ __forceinline__ Cplx<T> ld_table(const Cplx<T>* p) {
+  if constexpr (sizeof(T) == 8)
+    return Cplx<T>{__ldg(&p->re), __ldg(&p->im)};
+  else
+    return *p;
 }
 
 template <typename T>
@@ -765,7 +796,7 @@ __device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondAr
   Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
   Cplx<TP>* Lt = L0 + N * Nx;
   const int units = (Ny + 1) / 2 * N;
-  for (int u = X.vrank; u < units; u += X.vsize) {
+  for (int u = next_unit(X, units); u < units; u = next_unit(X, units)) {
     const int pr = u / N, a = u - pr * N;
     const int cy0 = 2 * pr, cy1 = cy0 + 1;
     const bool hasb = cy1 < Ny;
@@ -777,6 +808,7 @@ __device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondAr
     }
     __syncthreads();
     fft_lines(L0, Lt, N, Nx, P.log2x, P.twx, false, false);
+#pragma unroll 1
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
       const int km = k == 0 ? 0 : Nx - k;
       Cplx<TP> A[N], B[N];
@@ -794,7 +826,7 @@ __device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondAr
         Cplx<TP> ta{TP(0), TP(0)}, tb{TP(0), TP(0)};
 #pragma unroll
         for (int b = 0; b < N; ++b) {
-          const Cplx<TP> v = ld_cplx_ro(V + b * N + j);  // conj(v) * x
+          const Cplx<TP> v = ld_table(V + b * N + j);  // conj(v) * x
           ta.re = fma(v.re, A[b].re, fma(v.im, A[b].im, ta.re));
           ta.im = fma(v.re, A[b].im, fma(-v.im, A[b].re, ta.im));
           tb.re = fma(v.re, B[b].re, fma(v.im, B[b].im, tb.re));
@@ -806,6 +838,7 @@ __device__ __forceinline__ void spectral_rows_fwd(const Geom& G, const PrecondAr
     }
     __syncthreads();
   }
+  end_units(X, units);
 }
 
 // Phase 2, per unit (kx, j): DFT along y of S[kx][.][a][j] for every a, then per ky
@@ -816,7 +849,7 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
   Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
   Cplx<TP>* Lt = L0 + N * Ny;
   const TP scale = TP(1) / (TP(Nx) * TP(Ny));
-  for (int u = X.vrank; u < W * N; u += X.vsize) {
+  for (int u = next_unit(X, W * N); u < W * N; u = next_unit(X, W * N)) {
     const int kx = u / N, j = u - kx * N;
     const Cplx<TP>* Sk = P.S + (size_t)kx * Ny * N * N;
     for (int i = threadIdx.x; i < Ny * N; i += blockDim.x) {
@@ -826,17 +859,16 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
     __syncthreads();
     fft_lines(L0, Lt, N, Ny, P.log2y, P.twy, false, false);
     const TP lxj = P.lx[kx * N + j];
+#pragma unroll 1
     for (int ky = threadIdx.x; ky < Ny; ky += blockDim.x) {
       const Cplx<TP>* V = P.Vy + (size_t)ky * N * N;
-      // the n x n transform is read row by row from L1 in both directions (holding all of V
-      // in registers for both would spill)
       Cplx<TP> t[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         Cplx<TP> acc{TP(0), TP(0)};
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          const Cplx<TP> v = ld_cplx_ro(V + a * N + i), x = L0[a * Ny + ky];
+          const Cplx<TP> v = ld_table(V + a * N + i), x = L0[a * Ny + ky];
           acc.re = fma(v.re, x.re, fma(v.im, x.im, acc.re));
           acc.im = fma(v.re, x.im, fma(-v.im, x.re, acc.im));
         }
@@ -848,7 +880,7 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
       for (int a = 0; a < N; ++a) {
         Cplx<TP> acc{TP(0), TP(0)};
 #pragma unroll
-        for (int i = 0; i < N; ++i) acc = cadd(acc, cmul(ld_cplx_ro(V + a * N + i), t[i]));
+        for (int i = 0; i < N; ++i) acc = cadd(acc, cmul(ld_table(V + a * N + i), t[i]));
         L0[a * Ny + ky] = acc;
       }
     }
@@ -861,21 +893,21 @@ __device__ __forceinline__ void spectral_cols(const Geom& G, const PrecondArgs<T
     }
     __syncthreads();
   }
+  end_units(X, W * N);
 }
 
-// Phase 3: z~[cy, ., a, b] = inverse real DFT_x of sum_j Vx[kx][b][j] S[kx][cy][a][j]; returns
-// this block's share of r~ . z~ in acc.
+// Phase 3: z~[cy, ., a, b] = inverse real DFT_x of sum_j Vx[kx][b][j] S[kx][cy][a][j].
 template <typename TP, int N, typename TR>
-__device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondArgs<TP>& P, const TR* r,
-                                                  SolveCtx<TR>& X, TR& acc) {
+__device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondArgs<TP>& P, SolveCtx<TR>& X) {
   const int Nx = G.Nx, Ny = G.Ny, W = Nx / 2 + 1;
   Cplx<TP>* L0 = reinterpret_cast<Cplx<TP>*>(X.line0);
   Cplx<TP>* Lt = L0 + N * Nx;
   const int units = (Ny + 1) / 2 * N;
-  for (int u = X.vrank; u < units; u += X.vsize) {
+  for (int u = next_unit(X, units); u < units; u = next_unit(X, units)) {
     const int pr = u / N, a = u - pr * N;
     const int cy0 = 2 * pr, cy1 = cy0 + 1;
     const bool hasb = cy1 < Ny;
+#pragma unroll 1
     for (int k = threadIdx.x; k < W; k += blockDim.x) {
       const Cplx<TP>* V = P.Vx + (size_t)k * N * N;
       const Cplx<TP>* Sa = P.S + (((size_t)k * Ny + cy0) * N + a) * N;
@@ -892,7 +924,7 @@ __device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondAr
         Cplx<TP> A{TP(0), TP(0)}, B{TP(0), TP(0)};
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const Cplx<TP> v = ld_cplx_ro(V + b * N + j);
+          const Cplx<TP> v = ld_table(V + b * N + j);
           A = cadd(A, cmul(v, ta[j]));
           B = cadd(B, cmul(v, tb[j]));
         }
@@ -906,17 +938,12 @@ __device__ __forceinline__ void spectral_rows_inv(const Geom& G, const PrecondAr
     for (int i = threadIdx.x; i < Nx * N; i += blockDim.x) {
       const int cx = i / N, b = i - cx * N;
       const Cplx<TP> zv = L0[b * Nx + dft_slot(cx, P.log2x)];
-      const size_t g0 = (((size_t)cy0 * Nx + cx) * N + a) * N + b;
-      __stcg(P.z + g0, zv.re);
-      acc = fma(TR(zv.re), __ldcg(r + g0), acc);
-      if (hasb) {
-        const size_t g1 = (((size_t)cy1 * Nx + cx) * N + a) * N + b;
-        __stcg(P.z + g1, zv.im);
-        acc = fma(TR(zv.im), __ldcg(r + g1), acc);
-      }
+      __stcg(P.z + (((size_t)cy0 * Nx + cx) * N + a) * N + b, zv.re);
+      if (hasb) __stcg(P.z + (((size_t)cy1 * Nx + cx) * N + a) * N + b, zv.im);
     }
     __syncthreads();
   }
+  end_units(X, units);
 }
 
 // z~ = Ahat^+ r~ (spectral preconditioner): the three phases and the sum r~ . z~ (in every block).
@@ -927,8 +954,13 @@ __device__ __forceinline__ bool pc_spectral(const Geom& G, const PrecondArgs<TP>
   if (!solve_barrier(X)) return false;
   spectral_cols<TP, N, TR>(G, P, X);
   if (!solve_barrier(X)) return false;
+  spectral_rows_inv<TP, N, TR>(G, P, X);
+  if (!solve_barrier(X)) return false;
+  // r~ . z~ in a fixed order over the dofs (the units above were scheduled dynamically)
+  const size_t ndof = (size_t)G.Nx * G.Ny * N * N;
   TR acc = TR(0);
-  spectral_rows_inv<TP, N, TR>(G, P, r, X, acc);
+  for (size_t i = (size_t)X.vrank * blockDim.x + threadIdx.x; i < ndof; i += (size_t)X.vsize * blockDim.x)
+    acc = fma(TR(__ldcg(P.z + i)), __ldcg(r + i), acc);
   return reduce_all(X, acc, rz);
 }
 
@@ -1258,6 +1290,7 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
   X.sync = A.sync;
   X.part = A.part;
   X.phase = 0;
+  X.tbase = read_ticket<T>(A.sync);  // before the first barrier: no block has drawn yet
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)X.vsize * blockDim.x;
@@ -1468,6 +1501,7 @@ __device__ __forceinline__ void mixed_solve(const Ops2D<double, N>& Cd, const Op
   Xd.sync = A.sync;
   Xd.part = A.partd;
   Xd.phase = 0;
+  Xf.tbase = Xd.tbase = read_ticket<float>(A.sync);  // before the first barrier
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
   const size_t stride = (size_t)Xd.vsize * blockDim.x;
   int flags = 0, sweeps = 0;
