@@ -529,7 +529,10 @@ def main():
                                      "peak_source": peak_src,
                                      "traffic": measured_traffic("cg_kernel", args.workload, mname,
                                                                  precond=args.precond),
-                                     "bytes_per_dof": "16 + 32 (sweeps + 1) + 32 x inner iterations"}
+                                     "bytes_per_dof": "16 + 32 (sweeps + 1) + 32 x inner iterations",
+                                     "note": "HBM fraction by the refinement's algorithmic bytes; with one "
+                                             "inner iteration per solve the kernel is bound by its float64 "
+                                             "residual applications, not by HBM"}
             modes[mname] = entry
             ms_.close()
 

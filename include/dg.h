@@ -154,8 +154,11 @@ int dg_grid_set_tiles(dg_grid* g, int TY, int TX);
  * dg_spectral_symbol); z = A^+ r is a real 2D DFT of the n^2 node fields, n x n transforms per
  * wave vector, a division by the eigenvalue sums (the constant mode dropped) and the inverse
  * transforms.  CG then converges in one iteration in exact arithmetic (two or three in
- * floating point); the solution is returned with zero W-mean.  Errors: DG_ERR_ARG (also for
- * DG_PRECOND_TWOLEVEL and DG_PRECOND_SPECTRAL on a Dirichlet grid: both use periodic DFTs).
+ * floating point); the solution is returned with zero W-mean.  Its DFTs are radix-2 for cell
+ * counts that are powers of two and direct sums otherwise (a side that is not a power of two
+ * may have at most 256 cells).  Errors: DG_ERR_ARG (also for DG_PRECOND_TWOLEVEL and
+ * DG_PRECOND_SPECTRAL on a Dirichlet grid: both use periodic DFTs; and for DG_PRECOND_SPECTRAL
+ * with a side that is not a power of two above 256 cells).
  */
 int dg_grid_set_precond(dg_grid* g, int kind);
 

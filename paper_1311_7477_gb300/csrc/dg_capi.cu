@@ -599,6 +599,8 @@ int dg_grid_set_compensated_apply(dg_grid* g, int mode) {
 
 int dg_grid_get_compensated_apply(const dg_grid* g) { return g ? g->precise_apply : 0; }
 
+constexpr int kSpectralDirectMax = 256;  // longest non-power-of-two line of the spectral DFTs
+
 int dg_grid_set_precond(dg_grid* g, int kind) {
   if (!g) return fail(DG_ERR_ARG, "g is NULL");
   if (kind != DG_PRECOND_JACOBI && kind != DG_PRECOND_TWOLEVEL && kind != DG_PRECOND_SPECTRAL)
@@ -609,6 +611,12 @@ int dg_grid_set_precond(dg_grid* g, int kind) {
     return fail(DG_ERR_ARG, "the spectral preconditioner needs a periodic grid");
   if (kind == DG_PRECOND_SPECTRAL && g->pc.spectral_rc != DG_OK)
     return fail(DG_ERR_ARG, "the spectral preconditioner's tables could not be built for this grid");
+  // a side that is not a power of two takes the direct O(L^2) DFT per line: fine for small
+  // lines, far slower than CG with another preconditioner beyond a few hundred cells
+  if (kind == DG_PRECOND_SPECTRAL && ((g->pc.log2x < 0 && g->Nx > kSpectralDirectMax) ||
+                                      (g->pc.log2y < 0 && g->Ny > kSpectralDirectMax)))
+    return fail(DG_ERR_ARG, "the spectral preconditioner needs cell counts that are powers of two above %d",
+                kSpectralDirectMax);
   g->precond = kind;
   return DG_OK;
 }

@@ -163,3 +163,12 @@ def test_full_size_spectral(dg, prec):
     info = sim.status()
     assert info.status == 0
     assert info.cg_iters_last <= 8, info.cg_iters_last
+
+
+def test_spectral_rejects_long_non_power_of_two_lines(dg):
+    """A side that is not a power of two takes the direct DFT, allowed up to 256 cells."""
+    g = dg.Grid(300, 64, 2)
+    with pytest.raises(dg.DGError):
+        g.set_precond("spectral")
+    g2 = dg.Grid(200, 64, 2)
+    g2.set_precond("spectral")
