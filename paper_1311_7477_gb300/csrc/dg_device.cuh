@@ -509,7 +509,8 @@ __device__ __forceinline__ Cplx<T> csub(Cplx<T> a, Cplx<T> b) {
 // direct sum into tmp[0 .. count L)) as for dft_line.  Power-of-two L: with dif == false the
 // decimation-in-time form of dft_line (bit-reversed input, natural output); with dif == true
 // decimation in frequency (natural input, output in bit-reversed order: element k of the
-// transform at position dft_slot(k, log2L)).  Both take two radix-2 stages per pass.
+// transform at position dft_slot(k, log2L)).  Both take two radix-2 stages per pass, as one
+// radix-4 butterfly (three twiddle products per four values).
 template <typename T>
 __device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, int L, int log2L, const Cplx<T>* tw,
                                           bool inverse, bool dif) {
@@ -568,27 +569,29 @@ __device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, i
       half = 4;
       lh = 2;
     }
+    // two stages (spans half, 2 half) as one radix-4 butterfly with the three twiddles
+    // W^p, W^2p, W^3p (W = exp(-+ 2 pi i / 4 half), p the position in the group)
     for (; half < L; half <<= 2, lh += 2) {
-      const int s2 = L / (2 * half), s4 = L / (4 * half);
+      const int s4 = L / (4 * half);
       for (int t = tid; t < count * q; t += nth) {
         const int line = t >> (log2L - 2), tt = t & (q - 1);
         const int grp = tt >> lh, pos = tt & (half - 1);
         Cplx<T>* b = s + line * L + grp * 4 * half + pos;
-        Cplx<T> w2 = tw[pos * s2], w4 = tw[pos * s4];
+        Cplx<T> w1 = tw[pos * s4], w2 = tw[2 * pos * s4], w3 = tw[3 * pos * s4];
         if (inverse) {
+          w1.im = -w1.im;
           w2.im = -w2.im;
-          w4.im = -w4.im;
+          w3.im = -w3.im;
         }
-        const Cplx<T> a = b[0], bb = cmul(w2, b[half]);
-        const Cplx<T> c = b[2 * half], d = cmul(w2, b[3 * half]);
-        const Cplx<T> A1 = cadd(a, bb), B1 = csub(a, bb);
-        const Cplx<T> C1 = cmul(w4, cadd(c, d));
-        Cplx<T> D1 = cmul(w4, csub(c, d));
-        D1 = inverse ? Cplx<T>{-D1.im, D1.re} : Cplx<T>{D1.im, -D1.re};  // times -+ i
-        b[0] = cadd(A1, C1);
-        b[2 * half] = csub(A1, C1);
-        b[half] = cadd(B1, D1);
-        b[3 * half] = csub(B1, D1);
+        const Cplx<T> a = b[0], tb = cmul(w2, b[half]);
+        const Cplx<T> tc = cmul(w1, b[2 * half]), td = cmul(w3, b[3 * half]);
+        const Cplx<T> s1 = cadd(a, tb), s2 = csub(a, tb), s3 = cadd(tc, td);
+        Cplx<T> s4v = csub(tc, td);
+        s4v = inverse ? Cplx<T>{-s4v.im, s4v.re} : Cplx<T>{s4v.im, -s4v.re};  // times -+ i
+        b[0] = cadd(s1, s3);
+        b[2 * half] = csub(s1, s3);
+        b[half] = cadd(s2, s4v);
+        b[3 * half] = csub(s2, s4v);
       }
       __syncthreads();
     }
@@ -611,25 +614,26 @@ __device__ __forceinline__ void fft_lines(Cplx<T>* s, Cplx<T>* tmp, int count, i
         __syncthreads();
         continue;
       }
-      const int s4 = L / (4 * h), s2 = L / (2 * h);
+      // the two stages as one radix-4 butterfly with the three twiddles W^p, W^2p, W^3p
+      const int s4 = L / (4 * h);
       for (int t = tid; t < count * q; t += nth) {
         const int line = t >> (log2L - 2), tt = t & (q - 1);
         const int grp = tt >> lh, pos = tt & (h - 1);
         Cplx<T>* b = s + line * L + grp * 4 * h + pos;
-        Cplx<T> w4 = tw[pos * s4], w2 = tw[pos * s2];
+        Cplx<T> w1 = tw[pos * s4], w2 = tw[2 * pos * s4], w3 = tw[3 * pos * s4];
         if (inverse) {
-          w4.im = -w4.im;
+          w1.im = -w1.im;
           w2.im = -w2.im;
+          w3.im = -w3.im;
         }
         const Cplx<T> x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
-        const Cplx<T> y0 = cadd(x0, x2), y1 = cadd(x1, x3);
-        const Cplx<T> y2 = cmul(csub(x0, x2), w4);
-        Cplx<T> y3 = cmul(csub(x1, x3), w4);
-        y3 = inverse ? Cplx<T>{-y3.im, y3.re} : Cplx<T>{y3.im, -y3.re};  // w4^h = -+ i
-        b[0] = cadd(y0, y1);
-        b[h] = cmul(csub(y0, y1), w2);
-        b[2 * h] = cadd(y2, y3);
-        b[3 * h] = cmul(csub(y2, y3), w2);
+        const Cplx<T> u0 = cadd(x0, x2), u1 = cadd(x1, x3), u2 = csub(x0, x2);
+        Cplx<T> u3 = csub(x1, x3);
+        u3 = inverse ? Cplx<T>{-u3.im, u3.re} : Cplx<T>{u3.im, -u3.re};  // times -+ i
+        b[0] = cadd(u0, u1);
+        b[h] = cmul(w2, csub(u0, u1));
+        b[2 * h] = cmul(w1, cadd(u2, u3));
+        b[3 * h] = cmul(w3, csub(u2, u3));
       }
       __syncthreads();
     }
