@@ -775,6 +775,7 @@ void free_sim(dg_sim* s) {
   free_events(s);
   for (auto& p : s->omega) cudaFree(p);
   for (auto& p : s->psi) cudaFree(p);
+  for (auto& p : s->apsi) cudaFree(p);
   for (auto& p : s->R) cudaFree(p);
   cudaFree(s->stA);
   cudaFree(s->stB);
@@ -787,9 +788,10 @@ void free_sim(dg_sim* s) {
 // the persistent float64 CG kernel, or (DG_MIXED, DG_MIXED64) the float64-residual /
 // float32-CG refinement kernel.
 int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const double* xb, double cb, double* y,
-              cudaStream_t st) {
+              cudaStream_t st, const double* axa = nullptr, const double* axb = nullptr, double* ay = nullptr) {
   dg_grid* g = s->g;
   int rc;
+  if (s->fixed_iters > 0) axa = axb = ay = nullptr;  // parity mode: the plain operator applications
   if (s->precision == DG_FP64_PC32) {
     CgArgs<double, float> A{};
     A.omega = omega;
@@ -798,6 +800,9 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.ca = ca;
     A.cb = cb;
     A.x_unscaled = 0;
+    A.axa = axa;
+    A.axb = axb;
+    A.ay = ay;
     A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
@@ -815,6 +820,9 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.ca = ca;
     A.cb = cb;
     A.x_unscaled = 0;
+    A.axa = axa;
+    A.axb = axb;
+    A.ay = ay;
     A.y = y;
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
@@ -834,6 +842,9 @@ int sim_solve(dg_sim* s, const double* omega, const double* xa, double ca, const
     A.ca = ca;
     A.cb = cb;
     A.x_unscaled = 0;
+    A.axa = axa;
+    A.axb = axb;
+    A.ay = ay;
     A.v = CgVectors<double>{y, s->ws.r, s->ws.p0, s->ws.p1, s->ws.q};
     A.precond = g->precond;
     A.tol2 = s->tol * s->tol;
@@ -907,25 +918,37 @@ const double kAB[5][4] = {{0, 0, 0, 0},
                           {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0},
                           {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0}};
 
+// A stepper solve into psi slot `out` from the guess ca psi[a] + cb psi[b] (b < 0: none),
+// recycling the slots' operator products when they are known and keeping the result's.
+int sim_solve_slots(dg_sim* s, const double* omega, int a, double ca, int b, double cb, int out, cudaStream_t st) {
+  const bool rec = s->fixed_iters == 0 && s->apsi_ok[a] && (b < 0 || s->apsi_ok[b]);
+  s->apsi_ok[out] = false;
+  const int rc = sim_solve(s, omega, s->psi[a], ca, b < 0 ? nullptr : s->psi[b], cb, s->psi[out], st,
+                           rec ? s->apsi[a] : nullptr, rec && b >= 0 ? s->apsi[b] : nullptr, s->apsi[out]);
+  if (!rc) s->apsi_ok[out] = s->fixed_iters == 0;
+  return rc;
+}
+
 // One classical RK4 step (start-up of the multistep method).  k1 is kept as R^k.
 int sim_rk4_step(dg_sim* s, cudaStream_t st) {
   const double* w0 = s->omega[s->oc];
   double* w1 = s->omega[s->oc ^ 1];
   void* k1 = s->R[s->rfree];
-  double* PA = s->psi[s->p2];
-  double* PB = s->psi[s->p1];
+  const int sA = s->p2, sB = s->p1;
+  double* PA = s->psi[sA];
+  double* PB = s->psi[sB];
   const double* P0 = s->psi[s->p0];
   int rc;
   if ((rc = sim_rhs(s, P0, w0, w0, s->stA, k1, 0.5, 0, nullptr, nullptr, st))) return rc;
-  if ((rc = sim_solve(s, s->stA, P0, 1.0, nullptr, 0.0, PA, st))) return rc;
+  if ((rc = sim_solve_slots(s, s->stA, s->p0, 1.0, -1, 0.0, sA, st))) return rc;
   if ((rc = sim_rhs(s, PA, s->stA, w0, s->stB, s->k2, 0.5, 0, nullptr, nullptr, st))) return rc;
-  if ((rc = sim_solve(s, s->stB, PA, 1.0, nullptr, 0.0, PB, st))) return rc;
+  if ((rc = sim_solve_slots(s, s->stB, sA, 1.0, -1, 0.0, sB, st))) return rc;
   if ((rc = sim_rhs(s, PB, s->stB, w0, s->stA, s->k3, 1.0, 0, nullptr, nullptr, st))) return rc;
-  if ((rc = sim_solve(s, s->stA, PB, 1.0, nullptr, 0.0, PA, st))) return rc;
+  if ((rc = sim_solve_slots(s, s->stA, sB, 1.0, -1, 0.0, sA, st))) return rc;
   void* const hist[3] = {k1, s->k2, s->k3};
   const double ch[3] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0};
   if ((rc = sim_rhs(s, PA, s->stA, w0, w1, nullptr, 1.0 / 6.0, 3, hist, ch, st))) return rc;
-  if ((rc = sim_solve(s, w1, PA, 1.0, nullptr, 0.0, PB, st))) return rc;
+  if ((rc = sim_solve_slots(s, w1, sA, 1.0, -1, 0.0, sB, st))) return rc;
   // psi^{k+1} = PB (old p1 slot), psi^k stays p0: rotate (p0, p1, p2) <- (p1, p0, p2)
   std::swap(s->p0, s->p1);
   rotate_history(s);
@@ -946,7 +969,7 @@ int sim_ab3_step(dg_sim* s, cudaStream_t st) {
   const double ch[3] = {kAB[K][1], kAB[K][2], kAB[K][3]};
   int rc;
   if ((rc = sim_rhs(s, s->psi[s->p0], w0, w0, w1, Rk, kAB[K][0], K - 1, hist, ch, st))) return rc;
-  if ((rc = sim_solve(s, w1, s->psi[s->p0], 2.0, s->psi[s->p1], -1.0, s->psi[s->p2], st))) return rc;
+  if ((rc = sim_solve_slots(s, w1, s->p0, 2.0, s->p1, -1.0, s->p2, st))) return rc;
   const int np0 = s->p2, np1 = s->p0, np2 = s->p1;
   s->p0 = np0;
   s->p1 = np1;
@@ -1026,6 +1049,7 @@ int sim_new(dg_sim** sp, dg_grid* g, double D, double dt, int precision, double 
   auto alloc_all = [&]() -> int {
     for (auto& p : s->omega) CUDA_TRY(cudaMalloc(&p, bytes));
     for (auto& p : s->psi) CUDA_TRY(cudaMalloc(&p, bytes));
+    for (auto& p : s->apsi) CUDA_TRY(cudaMalloc(&p, bytes));
     for (auto& p : s->R) CUDA_TRY(cudaMalloc(&p, rbytes));
     CUDA_TRY(cudaMalloc(&s->stA, bytes));
     CUDA_TRY(cudaMalloc(&s->stB, bytes));
@@ -1062,9 +1086,11 @@ int dg_sim_create(dg_sim** sp, dg_grid* g, double D, double dt, int precision, d
                     ? DG_OK
                     : fail(DG_ERR_CUDA, "copy of omega0 failed");
   // psi^0 from a zero initial guess; psi^{-1} = psi^0 so the first extrapolation is psi^0.
-  if (!rc) rc = sim_solve(s, s->omega[0], nullptr, 0.0, nullptr, 0.0, s->psi[0], st);
-  if (!rc && cudaMemcpyAsync(s->psi[1], s->psi[0], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (!rc) rc = sim_solve(s, s->omega[0], nullptr, 0.0, nullptr, 0.0, s->psi[0], st, nullptr, nullptr, s->apsi[0]);
+  if (!rc && (cudaMemcpyAsync(s->psi[1], s->psi[0], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+              cudaMemcpyAsync(s->apsi[1], s->apsi[0], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
     rc = fail(DG_ERR_CUDA, "copy failed");
+  s->apsi_ok[0] = s->apsi_ok[1] = !rc;
   SolveStatus ss;
   if (!rc) rc = read_status(s->ws, &ss, st);
   if (!rc) rc = flags_to_status(ss.last_flags);
@@ -1149,6 +1175,7 @@ int dg_sim_set_state(dg_sim* s, long long step, const double* omega, const doubl
   cudaStream_t st = as_stream(stream);
   const size_t bytes = ndof_of(s->g) * sizeof(double);
   s->step = step;
+  s->apsi_ok[0] = s->apsi_ok[1] = s->apsi_ok[2] = false;
   CUDA_TRY(cudaMemcpyAsync(s->omega[s->oc], omega, bytes, cudaMemcpyDeviceToDevice, st));
   if (int rc = R_from_double(s, R1, s->R[s->r1], st)) return rc;
   if (int rc = R_from_double(s, R2, s->R[s->r2], st)) return rc;
@@ -1266,6 +1293,8 @@ int dg_sim_save(dg_sim* s, const char* path, void* stream) {
   h.max_sweeps = s->max_sweeps;
   h.precond = g->precond;
   h.bc = g->bc;
+  // reserved: bit 0 / 1 = the operator products of psi^k / psi^{k-1} follow the six fields
+  h.reserved = (s->apsi_ok[s->p0] ? 1 : 0) | (s->apsi_ok[s->p1] ? 2 : 0);
   h.step = s->step;
   h.Lx = g->Lx;
   h.Ly = g->Ly;
@@ -1278,9 +1307,12 @@ int dg_sim_save(dg_sim* s, const char* path, void* stream) {
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(DG_ERR_IO, "cannot open %s for writing", path);
   int rc = std::fwrite(&h, sizeof(h), 1, f) == 1 ? DG_OK : fail(DG_ERR_IO, "write failed");
-  // omega, the solver variables sqrt(W) psi^k and sqrt(W) psi^{k-1}, then R^{k-1..k-3}
-  const void* fields[6] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3]};
-  for (int i = 0; i < 6 && !rc; ++i) {
+  // omega, the solver variables sqrt(W) psi^k and sqrt(W) psi^{k-1}, then R^{k-1..k-3}, then
+  // the known operator products Ahat psi^k, Ahat psi^{k-1} (reserved bits)
+  const void* fields[8] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3],
+                           s->apsi[s->p0], s->apsi[s->p1]};
+  for (int i = 0; i < 8 && !rc; ++i) {
+    if (i >= 6 && !(h.reserved & (1 << (i - 6)))) continue;
     const double* src = static_cast<const double*>(fields[i]);
     if (cudaMemcpyAsync(host.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1311,7 +1343,8 @@ int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
     return fail(DG_ERR_ARG, "the grid (size, n, domain, tau, preconditioner, boundaries) differs from the saved one");
   }
   if (h.K < 1 || h.K > 4 || h.step < 0 || (h.bracket != DG_BRACKET_ARAKAWA && h.bracket != DG_BRACKET_NAIVE) ||
-      h.fixed_iters < 0 || h.max_sweeps < 1 || !(h.tol_in > 0.0 && h.tol_in < 1.0)) {
+      h.fixed_iters < 0 || h.max_sweeps < 1 || !(h.tol_in > 0.0 && h.tol_in < 1.0) || h.reserved < 0 ||
+      h.reserved > 3) {
     std::fclose(f);
     return fail(DG_ERR_IO, "corrupt header in %s", path);
   }
@@ -1328,9 +1361,11 @@ int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
   s->step = h.step;
   const size_t nd = ndof_of(g);
   std::vector<double> host(nd);
-  void* fields[6] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3]};
+  void* fields[8] = {s->omega[s->oc], s->psi[s->p0], s->psi[s->p1], s->R[s->r1], s->R[s->r2], s->R[s->r3],
+                     s->apsi[s->p0], s->apsi[s->p1]};
   int rc = DG_OK;
-  for (int i = 0; i < 6 && !rc; ++i) {
+  for (int i = 0; i < 8 && !rc; ++i) {
+    if (i >= 6 && !(h.reserved & (1 << (i - 6)))) continue;
     if (std::fread(host.data(), sizeof(double), nd, f) != nd) {
       rc = fail(DG_ERR_IO, "%s is truncated", path);
       break;
@@ -1348,6 +1383,8 @@ int dg_sim_load(dg_sim** sp, dg_grid* g, const char* path, void* stream) {
     delete s;
     return rc;
   }
+  s->apsi_ok[s->p0] = (h.reserved & 1) != 0;
+  s->apsi_ok[s->p1] = (h.reserved & 2) != 0;
   *sp = s;
   return DG_OK;
 }
@@ -1768,6 +1805,8 @@ int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream) {
   if (s->parts != 0) return fail(DG_ERR_ARG, "batched steps use the bracket of Eq. J");
   if (s->step < 2)
     if (int rc = dg_step(s, int(2 - s->step), stream)) return rc;  // RK4 start-up steps on their own
+  // the batched kernel moves the psi ring without the operator products
+  s->apsi_ok[0] = s->apsi_ok[1] = s->apsi_ok[2] = false;
   b->sims.push_back(s);
   b->dirty = true;
   return DG_OK;

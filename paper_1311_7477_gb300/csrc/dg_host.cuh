@@ -186,6 +186,11 @@ struct dg_sim {
   int oc;
   double* psi[3];  // scaled: sqrt(W) psi
   int p0, p1, p2;
+  // Ahat applied to each psi slot, valid where apsi_ok: every tolerance-stopped solve ends with
+  // the true residual of its result, whose operator product is kept, so that the next solve's
+  // initial residual b - Ahat (2 psi^k - psi^{k-1}) needs no operator application
+  double* apsi[3] = {nullptr, nullptr, nullptr};
+  bool apsi_ok[3] = {false, false, false};
   void* R[4];      // history ring: float64 (DG_FP64) or float32 (DG_MIXED)
   int r1, r2, r3, rfree;  // R^{k-1}, R^{k-2}, R^{k-3}, free slot
   int K = 3;              // steps of the Adams-Bashforth method (1..4)

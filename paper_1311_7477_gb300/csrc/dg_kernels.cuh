@@ -1006,7 +1006,7 @@ template <typename T, int N, typename TP = T>
 __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, const CgVectors<T>& V,
                                           const PrecondArgs<TP>* P, const RhsSource<T>& Bsrc, SolveCtx<T>& X,
                                           T& rr, T rz, T rhob, double tol2, int maxit, int fixed_iters, int& flags,
-                                          int max_restarts = kMaxRestarts, double floor2 = 0.0) {
+                                          int max_restarts = kMaxRestarts, double floor2 = 0.0, T* ay = nullptr) {
   constexpr int NN = N * N;
   const int ntiles = G.tilesX * G.tilesY;
   const size_t ndof = (size_t)G.Nx * G.Ny * NN;
@@ -1033,6 +1033,7 @@ __device__ __forceinline__ int cg_iterate(const Ops2D<T, N>& C, const Geom& G, c
             [&](size_t g, int k, T yv, T qv) {
               const T r = rhs_at<T, N>(C, Bsrc, g, k) - qv;
               __stcg(V.r + g, r);
+              if (ay) __stcg(ay + g, qv);
               rt = fma(r, r, rt);
               yt = fma(yv, yv, yt);
             });
@@ -1207,6 +1208,13 @@ struct CgArgs {
   const double* xb;     // sqrt(W) when x_unscaled
   double ca, cb;
   int x_unscaled;
+  // Recycled operator products (the stepper's extrapolated guesses): with axa non-null, Ahat y0
+  // = ca axa + cb axb (scaled space, x_unscaled == 0) replaces the setup's operator application,
+  // and with ay non-null the solve stores Ahat y of its final iterate there (from the verifying
+  // true-residual pass that ends every tolerance-stopped solve).
+  const T* axa;
+  const T* axb;
+  T* ay;
   CgVectors<T> v;
   int precond;          // kPrecondJacobi (W^-1: plain CG on the scaled system), kPrecondTwoLevel or kPrecondSpectral
   PrecondArgs<TP> pc;   // (TP = float: the preconditioner applied in float32)
@@ -1315,7 +1323,32 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
     }
   }
   // P1: y0, b, r0 = b - Ahat y0, rr0 = r0.r0, rhob = b.b.
-  {
+  if (A.axa) {  // Ahat y0 from the recycled products: a pointwise pass
+    T rrb = T(0), bbb = T(0);
+    const RhsSource<T> src{A.omega, A.rhs, wbar};
+    for (size_t g = (size_t)X.vrank * blockDim.x + threadIdx.x; g < ndof; g += stride) {
+      const int k = int(g % NN);
+      T y0 = T(0), ax = T(0);
+      if (A.xa) {
+        y0 = T(A.ca) * T(A.xa[g]);
+        ax = T(A.ca) * __ldcg(A.axa + g);
+      }
+      if (A.xb) {
+        y0 = fma(T(A.cb), T(A.xb[g]), y0);
+        ax = fma(T(A.cb), __ldcg(A.axb + g), ax);
+      }
+      __stcg(A.v.y + g, y0);
+      const T b = rhs_at<T, N>(C, src, g, k);
+      const T r = b - ax;
+      __stcg(A.v.r + g, r);
+      rrb = fma(r, r, rrb);
+      bbb = fma(b, b, bbb);
+    }
+    if (!reduce_all2(X, rrb, bbb, rr, rhob)) {
+      flags |= kFlagTimeout;
+      goto finish;
+    }
+  } else {
     T rrb = T(0), bbb = T(0);
     for (int t = X.vrank; t < ntiles; t += X.vsize) {
       cg_tile_apply<T, N>(
@@ -1350,7 +1383,7 @@ __device__ __forceinline__ void cg_solve(const Ops2D<T, N>& C, const Geom& G, co
       goto finish;
     }
     it = cg_iterate<T, N, TP>(C, G, A.v, pc ? &A.pc : nullptr, RhsSource<T>{A.omega, A.rhs, wbar}, X, rr, rz, rhob,
-                              A.tol2, A.maxit, A.fixed_iters, flags, kMaxRestarts, A.floor2);
+                              A.tol2, A.maxit, A.fixed_iters, flags, kMaxRestarts, A.floor2, A.ay);
     if (pc && !(flags & kFlagTimeout) && !project_mean<T, N>(C, G, A.v.y, A.sumW, X)) flags |= kFlagTimeout;
   }
 finish:
@@ -1410,6 +1443,9 @@ struct MixedArgs {
   const double* xb;
   double ca, cb;
   int x_unscaled;
+  const double* axa;   // recycled operator products, as in CgArgs
+  const double* axb;
+  double* ay;
   double* y;           // float64 solution (scaled space)
   double* psi_out;     // if non-null: psi = y / sqrt(W) at the end
   float* rf;           // float32 copy of the float64 residual (inner right-hand side)
@@ -1453,6 +1489,34 @@ template <int N>
 __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const Geom& G, const MixedArgs& A,
                                                double wbar, bool from_x0, SolveCtx<double>& X, double& rr,
                                                double& bb, double& yy) {
+  constexpr int NN = N * N;
+  if (from_x0 && A.axa) {  // Ahat y0 from the recycled products: a pointwise pass
+    const size_t ndof = (size_t)G.Nx * G.Ny * NN;
+    for (size_t g = (size_t)X.vrank * blockDim.x + threadIdx.x; g < ndof; g += (size_t)X.vsize * blockDim.x) {
+      const int k = int(g % NN);
+      double y0 = 0.0, ax = 0.0;
+      if (A.xa) {
+        y0 = A.ca * A.xa[g];
+        ax = A.ca * __ldcg(A.axa + g);
+      }
+      if (A.xb) {
+        y0 = fma(A.cb, A.xb[g], y0);
+        ax = fma(A.cb, __ldcg(A.axb + g), ax);
+      }
+      __stcg(A.y + g, y0);
+      if (A.ay) __stcg(A.ay + g, ax);
+      const double b = Cd.sw[k] * (A.omega[g] - wbar);
+      const double r = b - ax;
+      const float r32 = float(r);
+      __stcg(A.rf + g, r32);
+      __stcg(A.v.r + g, r32);
+      __stcg(A.v.y + g, 0.0f);
+      rr = fma(r, r, rr);
+      bb = fma(b, b, bb);
+      yy = fma(y0, y0, yy);
+    }
+    return;
+  }
   const int ntiles = G.tilesX * G.tilesY;
   for (int t = X.vrank; t < ntiles; t += X.vsize) {
     cg_tile_apply<double, N>(
@@ -1469,6 +1533,7 @@ __device__ __forceinline__ void mixed_residual(const Ops2D<double, N>& Cd, const
         [&](size_t g, int k, double yv, double qv) {
           const double b = Cd.sw[k] * (A.omega[g] - wbar);
           const double r = b - qv;
+          if (A.ay) __stcg(A.ay + g, qv);
           const float r32 = float(r);
           __stcg(A.rf + g, r32);
           __stcg(A.v.r + g, r32);
