@@ -1595,7 +1595,11 @@ BatchSim make_batch_sim(const dg_batch* bt, dg_sim* s) {
   b.precise_apply = g->precise_apply;
   b.keep_mean = g->bc;
   for (int i = 0; i < 2; ++i) b.omega[i] = s->omega[i];
-  for (int i = 0; i < 3; ++i) b.psi[i] = s->psi[i];
+  for (int i = 0; i < 3; ++i) {
+    b.psi[i] = s->psi[i];
+    b.apsi[i] = s->apsi[i];
+    b.apsi_ok[i] = s->apsi_ok[i] ? 1 : 0;
+  }
   for (int i = 0; i < 4; ++i) b.R[i] = s->R[i];
   b.oc = s->oc;
   b.p0 = s->p0;
@@ -1740,6 +1744,7 @@ void batch_advance_host(dg_batch* b, int nsteps) {
       if (s->batch_limit > 0 && s->step >= s->batch_limit) break;
       s->oc ^= 1;
       const int p0 = s->p0, p1 = s->p1, p2 = s->p2;
+      s->apsi_ok[p2] = s->fixed_iters == 0;
       s->p0 = p2;
       s->p1 = p0;
       s->p2 = p1;
@@ -1805,8 +1810,6 @@ int dg_batch_admit(dg_batch* b, dg_sim* s, void* stream) {
   if (s->parts != 0) return fail(DG_ERR_ARG, "batched steps use the bracket of Eq. J");
   if (s->step < 2)
     if (int rc = dg_step(s, int(2 - s->step), stream)) return rc;  // RK4 start-up steps on their own
-  // the batched kernel moves the psi ring without the operator products
-  s->apsi_ok[0] = s->apsi_ok[1] = s->apsi_ok[2] = false;
   b->sims.push_back(s);
   b->dirty = true;
   return DG_OK;

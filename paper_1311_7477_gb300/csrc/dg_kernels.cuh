@@ -1729,6 +1729,8 @@ struct BatchSim {
   const void* ops_k;               // device copy of OpsK<df, n> (double-float CG operator)
   double* omega[2];
   double* psi[3];                  // sqrt(W) psi
+  double* apsi[3];                 // Ahat psi of each slot, valid where apsi_ok (see dg_sim)
+  int apsi_ok[3];
   void* R[4];                      // right-hand-side history (float64)
   int oc, p0, p1, p2, r1, r2, r3, rfree;  // ring indices, advanced by the kernel
   long long step;
@@ -1820,6 +1822,8 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
                                       smem_all + table_bytes<Ops2D<double, N>>() + table_bytes<Ops2D<float, N>>());
   const bool pc = S.precond == kPrecondTwoLevel;  // the cell blocks are staged
   const int Lmax = max(S.Gc.Nx, S.Gc.Ny);
+  // the initial residual from the kept operator products (as in the single-simulation stepper)
+  const bool rec = S.fixed_iters == 0 && __ldcg(&Sp->apsi_ok[p0]) && __ldcg(&Sp->apsi_ok[p1]);
   if (S.precision == 0) {
     CgArgs<double> A{};
     A.omega = S.omega[oc ^ 1];
@@ -1827,6 +1831,11 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.xb = S.psi[p1];
     A.ca = 2.0;
     A.cb = -1.0;
+    if (rec) {
+      A.axa = S.apsi[p0];
+      A.axb = S.apsi[p1];
+    }
+    if (S.fixed_iters == 0) A.ay = S.apsi[p2];
     A.v = CgVectors<double>{S.psi[p2], S.r, S.p0v, S.p1v, S.q};
     A.precond = S.precond;
     A.pc = S.pc;
@@ -1854,6 +1863,11 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
     A.xb = S.psi[p1];
     A.ca = 2.0;
     A.cb = -1.0;
+    if (rec) {
+      A.axa = S.apsi[p0];
+      A.axb = S.apsi[p1];
+    }
+    if (S.fixed_iters == 0) A.ay = S.apsi[p2];
     A.y = S.psi[p2];
     A.rf = S.rf;
     A.v = CgVectors<float>{S.fe, S.fr, S.fp0, S.fp1, S.fq};
@@ -1890,6 +1904,7 @@ __device__ __noinline__ bool batch_step(BatchSim* Sp, const BatchGroup& grp, int
   // every block has finished the solve before the rings move
   if (!grid_barrier(grp.sync, s_flag, grp.nblocks)) return false;
   if (vrank == 0 && threadIdx.x == 0) {
+    Sp->apsi_ok[p2] = S.fixed_iters == 0 ? 1 : 0;
     Sp->oc = oc ^ 1;
     Sp->p0 = p2;
     Sp->p1 = p0;
